@@ -1,0 +1,174 @@
+/*
+ * lnr.h -- C ABI of the GB300 render path of "Real-time Neural Rendering of LiDAR Point
+ * Clouds" (arXiv 2502.11618): a coloured multi-scan LiDAR cloud is partitioned by a
+ * uniform grid, culled against the view frustum, projected as 1x1 pixels into an RGBDA
+ * image, pruned by the depth-guided filter and turned into the output frame by a
+ * fully convolutional U-Net.
+ *
+ * Conventions shared by every call:
+ *  - All pointers are plain host pointers unless an argument says "device".  Input
+ *    buffers belong to the caller; the library copies what it needs during the call and
+ *    keeps no pointer to them.  Output buffers are allocated by the caller.
+ *  - Images are row-major, pixel (u, v) at index v*W + u; multi-channel images are
+ *    interleaved (HWC).  Batched images are view-major (NHWC).
+ *  - Every call returns an lnr_status.  No call aborts the process.  After an error,
+ *    lnr_last_error() describes it.
+ *  - A context owns one CUDA device and one stream; its calls are not thread-safe,
+ *    except lnr_submit / lnr_poll / lnr_serve_stats, which may be called from any
+ *    thread.
+ */
+#ifndef LNR_H
+#define LNR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lnr_ctx lnr_ctx;
+
+typedef enum {
+    LNR_OK = 0,
+    LNR_E_ARG = -1,      /* an argument is out of range, NULL or not finite */
+    LNR_E_STATE = -2,    /* calls out of order (render before build_grid / set_unet) */
+    LNR_E_OOM = -3,      /* device memory or the memory budget is exhausted */
+    LNR_E_CUDA = -4,     /* a CUDA call failed */
+    LNR_E_TIMEOUT = -5,  /* a bounded device or host wait ran out */
+    LNR_E_BUSY = -6      /* lnr_poll: the request is not finished yet */
+} lnr_status;
+
+typedef enum { LNR_FP32 = 0, LNR_BF16 = 1, LNR_FP8 = 2 } lnr_precision;
+
+/* A view: world-to-camera rotation R (row-major 3x3; camera x right, y down, z forward)
+ * and camera centre C in world coordinates.  Both in FP64: with georeferenced clouds the
+ * camera-relative geometry is formed in FP64 on the host before any FP32 rounding. */
+typedef struct {
+    double R[9];
+    double C[3];
+} lnr_view;
+
+/* Pinhole intrinsics (pixels) and the depth range; a point is drawn when
+ * znear < z < zfar.  zfar also normalises the depth channel of the U-Net input. */
+typedef struct {
+    float fx, fy, cx, cy, znear, zfar;
+} lnr_intrinsics;
+
+/* U-Net shape: `levels` resolution levels with ch[l] channels, in_ch = 5 (RGBDA),
+ * out_ch = 3 (RGB); has_bn = 1 when the weight file carries batch-norm statistics for the
+ * encoder convolutions. */
+typedef struct {
+    int levels;
+    int ch[8];
+    int in_ch;
+    int out_ch;
+    int has_bn;
+} lnr_unet_desc;
+
+/* Stages that lnr_render_stage can stop after (parity and debugging taps). */
+typedef enum {
+    LNR_STAGE_KEYS = 0,       /* uint64 [H*W]: (float bits of z << 32 | sorted position), ~0 = empty */
+    LNR_STAGE_RGBDA_RAW = 1,  /* 8 bytes per pixel: float z (+inf empty), uint8 r, g, b, A */
+    LNR_STAGE_FILTERED = 2,   /* float [H*W]: kept depth, +inf where empty or filtered out */
+    LNR_STAGE_UNET_IN = 3,    /* float [H*W*5]: r/255, g/255, b/255, z/zfar, A (zero where A = 0) */
+    LNR_STAGE_CULL = 4        /* uint64 [2]: visible non-empty cells, visible points */
+} lnr_stage;
+
+/* Create a context on CUDA device `device`.  cuda_stream (nullable) is a cudaStream_t the
+ * context issues its work on; NULL makes the context create its own stream. */
+lnr_status lnr_create(lnr_ctx** out, int device, void* cuda_stream);
+lnr_status lnr_destroy(lnr_ctx* ctx);
+
+/* Last error message of this context ("" when none).  Valid until the next call. */
+const char* lnr_last_error(lnr_ctx* ctx);
+
+/* Upload a cloud (Sec. 1: merged multi-scanner coloured points).  xyz: n x 3 FP64 world
+ * coordinates; rgb: n x 3 uint8; scan_id: n uint8 source-scanner index (nullable: 0).
+ * Invalidates any grid built before.  n must be in [1, 2^32 - 1]. */
+lnr_status lnr_load_cloud(lnr_ctx* ctx, const double* xyz, const uint8_t* rgb,
+                          const uint8_t* scan_id, uint64_t n);
+
+/* Uniform-grid partition of the loaded cloud (Sec. 1; Sec. 3, "Point Cloud
+ * Projection"), built on the device: grid origin g0 = floor(min/cell)*cell, stable
+ * counting sort of the points by cell id (k*dy + j)*dx + i, and per point an FP32 offset to
+ * its cell's FP64 origin.  cell_size > 0; at most 2^31 cells. */
+lnr_status lnr_build_grid(lnr_ctx* ctx, double cell_size);
+
+/* Grid summary: out_g0[3] (FP64 origin), out_dims[3] (cells per axis); nullable each. */
+lnr_status lnr_grid_info(lnr_ctx* ctx, double* out_g0, int32_t* out_dims);
+
+/* Load the U-Net (Fig. 1; Sec. 3, "U-Net Reconstruction").  weights: n_floats FP32 values;
+ * for every convolution in network order (enc0a, enc0b, ..., the bottleneck pair, then
+ * dec(L-2)a, dec(L-2)b, ..., dec0a, dec0b) its OIHW weight then its bias; then the 1x1 head
+ * (OIHW, bias); then, if has_bn, (gamma, beta, mean, var) per encoder convolution (folded
+ * into that convolution here, eps 1e-5).  A decoder "a" convolution reads the skip
+ * tensor's channels first, the nearest-upsampled deeper tensor's after.  The weights are
+ * converted for every precision; `precision` selects the one lnr_render uses. */
+lnr_status lnr_set_unet(lnr_ctx* ctx, const lnr_unet_desc* desc, const float* weights,
+                        size_t n_floats, lnr_precision precision);
+
+/* Select the U-Net precision for later renders (weights must be loaded). */
+lnr_status lnr_set_precision(lnr_ctx* ctx, lnr_precision precision);
+
+/* Render one frame (Fig. 1): cull, splat, filter (Fig. 2) with n_levels min-pool levels
+ * and filter_strength fs, U-Net.  out_rgb: H*W*3 FP32 in [0, 1], HWC; host memory, or
+ * device memory when out_on_device != 0 (then the call returns without waiting for the
+ * GPU; the result is complete when the context's stream reaches it).
+ * Errors: LNR_E_STATE before build_grid / set_unet; LNR_E_ARG when W or H is not a
+ * positive multiple of 2^(levels-1), n_levels is outside [0, floor(log2(min(W, H)))] or
+ * above 6, fs is negative or NaN, or the view is not finite. */
+lnr_status lnr_render(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                      int H, int n_levels, float fs, float* out_rgb, int out_on_device);
+
+/* The same path stopped after `stage`; `out` (host, or device when out_on_device) receives
+ * the buffer lnr_stage describes.  Needs set_unet only for no stage. */
+lnr_status lnr_render_stage(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr,
+                            int W, int H, int n_levels, float fs, int stage, void* out,
+                            int out_on_device);
+
+/* Render nviews views of one resolution in one pass: every view's splat, filter and
+ * U-Net run batched (the U-Net on an NHWC batch).  views, intr and fs are arrays of
+ * nviews; out_rgb holds nviews*H*W*3 floats, view-major.  Same errors as lnr_render. */
+lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
+                            const lnr_intrinsics* intr, int W, int H, int n_levels,
+                            const float* fs, float* out_rgb, int out_on_device);
+
+/* ---- serving: continuous batching of render requests ------------------------------ */
+
+/* Start the serving loop: up to max_batch requests of one resolution per launch, up to
+ * `slots` launches in flight on separate streams, admission bounded by the activation
+ * bytes of the requests in flight (lnr_set_memory_budget; 0 = no bound).  Uses the
+ * precision selected by set_unet / set_precision. */
+lnr_status lnr_serve_start(lnr_ctx* ctx, int max_batch, int slots);
+lnr_status lnr_serve_stop(lnr_ctx* ctx);
+lnr_status lnr_set_memory_budget(lnr_ctx* ctx, size_t bytes);
+
+/* Queue one render request; *ticket identifies it.  Thread-safe.  Arguments as
+ * lnr_render; they are copied. */
+lnr_status lnr_submit(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                      int H, int n_levels, float fs, uint64_t* ticket);
+
+/* Result of a request: LNR_E_BUSY until it is done, then copies H*W*3 floats to out_rgb
+ * (host, nullable) and its latency (completion minus submission, seconds) to
+ * *latency_s (nullable), and forgets the request.  Thread-safe. */
+lnr_status lnr_poll(lnr_ctx* ctx, uint64_t ticket, float* out_rgb, double* latency_s);
+
+/* Serving counters: out[0] requests done, out[1] launches, out[2] largest batch,
+ * out[3] peak activation bytes in flight.  Thread-safe. */
+lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[4]);
+
+/* ---- measurement ------------------------------------------------------------------- */
+
+/* Device time (ms) of each stage of the most recent lnr_render / lnr_render_batch with
+ * timing enabled: out[0] cull, out[1] splat, out[2] resolve+pyramid, out[3] upsample and
+ * pack, out[4] U-Net, out[5] whole frame; out[6] the dominant conv layer's time, out[7] the
+ * number of kernels launched.  Timing adds CUDA events to the stream; enable = 0 removes
+ * them. */
+lnr_status lnr_set_timing(lnr_ctx* ctx, int enable);
+lnr_status lnr_get_timing(lnr_ctx* ctx, double out[8]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LNR_H */

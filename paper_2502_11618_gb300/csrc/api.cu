@@ -1,0 +1,511 @@
+// C ABI of the render path (include/lnr.h): context, cloud upload, grid build, U-Net
+// loading, the FP64 host composition of each view, and the per-frame launch sequence.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "lnr_internal.h"
+
+namespace lnr {
+
+constexpr float kKeepRel = 0.05f;  // keep tolerance per unit of filter_strength
+constexpr double kBnEps = 1e-5;
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+lnr_status fail(lnr_ctx* c, lnr_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+lnr_status cuda_fail(lnr_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LNR_E_OOM : LNR_E_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void Workspace::release() {
+    DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_cell, &vis_pref, &vis_tot, &keys,
+                   &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
+    for (DBuf* b : all) b->release();
+    for (auto& a : act) a.release();
+    if (pinned_view.p) cudaFreeHost(pinned_view.p);
+    pinned_view.p = nullptr;
+    pinned_view.bytes = 0;
+    for (auto& e : ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+}
+
+// FP64 composition of the view with the grid (once per view, on the host): the anchor
+// cell holds the camera; d0 = R (origin(anchor) - C) and the grid steps R (cell e_k) are
+// formed in FP64 and rounded once, so georeferenced coordinates keep their precision.
+static void compose_view(const lnr_ctx* c, const lnr_view& v, const lnr_intrinsics& in, float fs, ViewDev& o) {
+    double rel[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = std::floor((v.C[a] - c->g0[a]) / c->cell);
+        if (f < 0.0) f = 0.0;
+        if (f > (double)(c->dims[a] - 1)) f = (double)(c->dims[a] - 1);
+        o.anchor[a] = (int32_t)f;
+        rel[a] = (c->g0[a] + (double)o.anchor[a] * c->cell) - v.C[a];
+    }
+    for (int r = 0; r < 3; ++r) {
+        double acc = v.R[3 * r] * rel[0];
+        acc = acc + v.R[3 * r + 1] * rel[1];
+        acc = acc + v.R[3 * r + 2] * rel[2];
+        o.d0[r] = (float)acc;
+        for (int k = 0; k < 3; ++k) o.s[3 * k + r] = (float)(v.R[3 * r + k] * c->cell);
+    }
+    for (int e = 0; e < 9; ++e) o.Rf[e] = (float)v.R[e];
+    o.fx = in.fx; o.fy = in.fy; o.cx = in.cx; o.cy = in.cy; o.znear = in.znear; o.zfar = in.zfar;
+    const float prod = fs * kKeepRel;
+    o.S = 1.0f + prod;
+    o.inv_pad = 0.f;
+}
+
+static bool finite_view(const lnr_view& v) {
+    for (double x : v.R) if (!std::isfinite(x)) return false;
+    for (double x : v.C) if (!std::isfinite(x)) return false;
+    return true;
+}
+
+static lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in,
+                                   int W, int H, int nlev, const float* fs, bool need_unet) {
+    if (!c->grid_ok) return fail(c, LNR_E_STATE, "render before build_grid");
+    if (need_unet && !c->unet_ok) return fail(c, LNR_E_STATE, "render before set_unet");
+    if (nviews < 1 || !views || !in || !fs) return fail(c, LNR_E_ARG, "null view, intrinsics or strength");
+    if (W < 1 || H < 1 || (int64_t)W * H > (1ll << 31)) return fail(c, LNR_E_ARG, "bad image size");
+    if (need_unet) {
+        const int m = 1 << (c->unet.levels - 1);
+        if (W % m || H % m) return fail(c, LNR_E_ARG, "W and H must be multiples of 2^(levels-1)");
+    }
+    int maxl = 0;
+    while ((2 << maxl) <= std::min(W, H)) ++maxl;
+    if (nlev < 0 || nlev > std::min(maxl, kMaxLevels))
+        return fail(c, LNR_E_ARG, "n_levels outside [0, min(6, floor(log2(min(W, H))))]");
+    for (int i = 0; i < nviews; ++i) {
+        if (!(fs[i] >= 0.0f)) return fail(c, LNR_E_ARG, "filter_strength must be >= 0 and not NaN");
+        if (!finite_view(views[i])) return fail(c, LNR_E_ARG, "view is not finite");
+        const lnr_intrinsics& k = in[i];
+        if (!(std::isfinite(k.fx) && std::isfinite(k.fy) && std::isfinite(k.cx) && std::isfinite(k.cy) &&
+              k.znear > 0.0f && k.zfar > k.znear && std::isfinite(k.zfar)))
+            return fail(c, LNR_E_ARG, "bad intrinsics");
+    }
+    return LNR_OK;
+}
+
+// Size every per-frame buffer for B views of W x H with nlev pyramid levels.
+static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int H, int nlev) {
+    cudaError_t e;
+    const size_t P = (size_t)W * H;
+    const int nb = cull_blocks(c->ncells);
+    const size_t pf = pyramid_floats(W, H, kMaxLevels);
+    if ((e = ws.view.ensure(sizeof(ViewDev) * B)) || (e = ws.cull_flag.ensure(4 * c->ncells * B)) ||
+        (e = ws.cull_cnt.ensure(4 * c->ncells * B)) || (e = ws.cull_bsum.ensure(8 * (size_t)nb * B)) ||
+        (e = ws.vis_cell.ensure(4 * c->ncells * B)) || (e = ws.vis_pref.ensure(4 * c->ncells * B)) ||
+        (e = ws.vis_tot.ensure(8 * B)) || (e = ws.depth.ensure(4 * P * B)) || (e = ws.rgba.ensure(4 * P * B)) ||
+        (e = ws.pyr_m.ensure(4 * pf * B)) || (e = ws.pyr_u.ensure(4 * pf * B)) || (e = ws.u0.ensure(4 * P * B)) ||
+        (e = ws.out.ensure(12 * P * B)))
+        return e;
+    const bool new_keys = ws.keys.bytes < 8 * P * B;
+    if ((e = ws.keys.ensure(8 * P * B))) return e;
+    if (new_keys) ws.keys_dirty = true;
+    if (ws.pinned_view.bytes < sizeof(ViewDev) * B) {
+        if (ws.pinned_view.p) cudaFreeHost(ws.pinned_view.p);
+        if ((e = cudaMallocHost(&ws.pinned_view.p, sizeof(ViewDev) * B))) return e;
+        ws.pinned_view.bytes = sizeof(ViewDev) * B;
+    }
+    if (!ws.ev[0])
+        for (auto& ev : ws.ev)
+            if ((e = cudaEventCreate(&ev))) return e;
+    ws.B = B;
+    ws.W = W;
+    ws.H = H;
+    ws.nlev = nlev;
+    return cudaSuccess;
+}
+
+// Enqueue one batch on `st`: params upload, cull, splat, resolve + pyramid, upsampling,
+// U-Net.  stage < 0 runs the whole frame into ws.out; otherwise stops after that stage.
+static void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec,
+                          bool timed) {
+    cudaEvent_t* ev = ws.ev;
+    auto mark = [&](int i) {
+        if (timed) cudaEventRecord(ev[i], st);
+    };
+    mark(0);
+    cudaMemcpyAsync(ws.view.p, ws.pinned_view.p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    if (ws.keys_dirty) launch_clear_keys(ws, st);
+    launch_cull(c, ws, st);
+    mark(1);
+    if (stage == LNR_STAGE_CULL) return;
+    launch_splat(c, ws, st);
+    mark(2);
+    if (stage == LNR_STAGE_KEYS) {
+        ws.keys_dirty = true;  // the resolve that would clear the keys does not run
+        return;
+    }
+    launch_resolve_pyramid(c, ws, st);
+    mark(3);
+    if (stage == LNR_STAGE_RGBDA_RAW) return;
+    const int kind = (stage >= 0) ? 0 : unet_in_kind(prec);
+    void* unet_in = ws.act[4 * kMaxUnetLevels].p;
+    for (int l = ws.nlev - 1; l >= 1; --l) launch_upsample(c, ws, l, nullptr, 2, false, st);
+    launch_upsample(c, ws, 0, unet_in, kind, stage == LNR_STAGE_FILTERED, st);
+    mark(4);
+    if (stage >= 0) return;
+    unet_forward(c, ws, prec, unet_in, ws.out.as<float>(), st, nullptr);
+    mark(5);
+}
+
+static lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in,
+                                int W, int H, int nlev, const float* fs) {
+    cudaError_t e = ensure_ws(c, ws, B, W, H, nlev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "workspace");
+    e = ws.act[4 * kMaxUnetLevels].ensure((size_t)B * W * H * 8 * 4 + 256);
+    if (e != cudaSuccess) return cuda_fail(c, e, "U-Net input");
+    ViewDev* hv = ws.pinned_view.as<ViewDev>();
+    // the pinned block may still feed an earlier launch on this stream
+    e = cudaStreamSynchronize(ws.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    for (int i = 0; i < B; ++i) compose_view(c, views[i], in[i], fs[i], hv[i]);
+    return LNR_OK;
+}
+
+static void read_timing(lnr_ctx* c, Workspace& ws) {
+    float ms;
+    for (int i = 0; i < 5; ++i) {
+        cudaEventElapsedTime(&ms, ws.ev[i], ws.ev[i + 1]);
+        c->times[i] = ms;
+    }
+    cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[5]);
+    c->times[5] = ms;
+}
+
+static lnr_status finish_output(lnr_ctx* c, Workspace& ws, float* out, size_t nfloat, int on_device) {
+    cudaError_t e = cudaMemcpyAsync(out, ws.out.p, nfloat * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ws.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output copy");
+    if (!on_device || c->timing) {
+        e = cudaStreamSynchronize(ws.stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "render");
+    }
+    if (c->timing) read_timing(c, ws);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
+    return LNR_OK;
+}
+
+}  // namespace lnr
+
+using namespace lnr;
+
+extern "C" {
+
+lnr_status lnr_create(lnr_ctx** out, int device, void* cuda_stream) {
+    if (!out) return LNR_E_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return LNR_E_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return LNR_E_CUDA;
+    lnr_ctx* c = new lnr_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return LNR_E_CUDA;
+        }
+        c->own_stream = true;
+    }
+    c->ws.stream = c->stream;
+    *out = c;
+    return LNR_OK;
+}
+
+lnr_status lnr_destroy(lnr_ctx* c) {
+    if (!c) return LNR_E_ARG;
+    cudaSetDevice(c->device);
+    lnr_serve_stop(c);
+    cudaStreamSynchronize(c->stream);
+    c->ws.release();
+    DBuf* all[] = {&c->xyz, &c->rgb, &c->scan, &c->cell_start, &c->ox, &c->oy, &c->oz, &c->rgbs};
+    for (DBuf* b : all) b->release();
+    for (auto& L : c->unet.convs) {
+        if (L.w32) cudaFree(L.w32);
+        if (L.b32) cudaFree(L.b32);
+        if (L.wtc) cudaFree(L.wtc);
+        if (L.wscale) cudaFree(L.wscale);
+    }
+    if (c->unet.head_w) cudaFree(c->unet.head_w);
+    if (c->unet.head_b) cudaFree(c->unet.head_b);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return LNR_OK;
+}
+
+const char* lnr_last_error(lnr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+lnr_status lnr_load_cloud(lnr_ctx* c, const double* xyz, const uint8_t* rgb, const uint8_t* scan_id, uint64_t n) {
+    if (!c) return LNR_E_ARG;
+    if (!xyz || !rgb) return fail(c, LNR_E_ARG, "null xyz or rgb");
+    if (n < 1 || n > 0xffffffffull) return fail(c, LNR_E_ARG, "point count outside [1, 2^32-1]");
+    cudaSetDevice(c->device);
+    for (uint64_t i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(xyz[i])) return fail(c, LNR_E_ARG, "non-finite coordinate");
+    cudaError_t e;
+    c->grid_ok = false;
+    if ((e = c->xyz.ensure(24 * n)) || (e = c->rgb.ensure(3 * n)) || (scan_id && (e = c->scan.ensure(n))))
+        return cuda_fail(c, e, "cloud upload");
+    if (!scan_id) c->scan.release();
+    if ((e = cudaMemcpy(c->xyz.p, xyz, 24 * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->rgb.p, rgb, 3 * n, cudaMemcpyHostToDevice)) ||
+        (scan_id && (e = cudaMemcpy(c->scan.p, scan_id, n, cudaMemcpyHostToDevice))))
+        return cuda_fail(c, e, "cloud upload");
+    c->n = n;
+    c->cloud_gen++;
+    return LNR_OK;
+}
+
+lnr_status lnr_build_grid(lnr_ctx* c, double cell) {
+    if (!c) return LNR_E_ARG;
+    if (!c->n) return fail(c, LNR_E_STATE, "build_grid before load_cloud");
+    if (!(cell > 0.0) || !std::isfinite(cell)) return fail(c, LNR_E_ARG, "cell size must be > 0");
+    cudaSetDevice(c->device);
+    DBuf tmp;
+    cudaError_t e = tmp.ensure(1024 * 6 * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "grid");
+    double lohi[6];
+    e = grid_bbox(c->xyz.as<double>(), c->n, tmp.as<double>(), lohi, c->stream);
+    tmp.release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "grid bounds");
+    double total = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        c->g0[a] = std::floor(lohi[a] / cell) * cell;
+        double d = std::floor((lohi[3 + a] - c->g0[a]) / cell) + 1.0;
+        if (d > 2147483647.0) return fail(c, LNR_E_ARG, "too many cells");
+        c->dims[a] = (int32_t)d;
+        total *= d;
+    }
+    if (total > 2147483647.0) return fail(c, LNR_E_ARG, "too many cells (> 2^31)");
+    c->cell = cell;
+    c->ncells = (int64_t)total;
+    e = grid_build(c, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "grid build");
+    c->grid_ok = true;
+    c->cloud_gen++;
+    c->ws.keys_dirty = true;
+    return LNR_OK;
+}
+
+lnr_status lnr_grid_info(lnr_ctx* c, double* g0, int32_t* dims) {
+    if (!c) return LNR_E_ARG;
+    if (!c->grid_ok) return fail(c, LNR_E_STATE, "no grid");
+    if (g0) std::memcpy(g0, c->g0, sizeof(c->g0));
+    if (dims) std::memcpy(dims, c->dims, sizeof(c->dims));
+    return LNR_OK;
+}
+
+lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size_t n_floats, lnr_precision prec) {
+    if (!c) return LNR_E_ARG;
+    if (!d || !w) return fail(c, LNR_E_ARG, "null descriptor or weights");
+    if (d->levels < 1 || d->levels > kMaxUnetLevels) return fail(c, LNR_E_ARG, "levels outside [1, 8]");
+    if (d->in_ch != 5 || d->out_ch < 1 || d->out_ch > 4) return fail(c, LNR_E_ARG, "in_ch must be 5, out_ch in [1, 4]");
+    if (prec < LNR_FP32 || prec > LNR_FP8) return fail(c, LNR_E_ARG, "bad precision");
+    for (int l = 0; l < d->levels; ++l)
+        if (d->ch[l] < 16 || d->ch[l] > 256 || d->ch[l] % 16) return fail(c, LNR_E_ARG, "channels must be multiples of 16 in [16, 256]");
+    const int L = d->levels;
+    // count and locate
+    size_t need = 0;
+    int cin = d->in_ch;
+    std::vector<std::pair<int, int>> shp;  // (cout, cin)
+    for (int l = 0; l < L; ++l) {
+        shp.push_back({d->ch[l], cin});
+        shp.push_back({d->ch[l], d->ch[l]});
+        cin = d->ch[l];
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        shp.push_back({d->ch[l], d->ch[l] + d->ch[l + 1]});
+        shp.push_back({d->ch[l], d->ch[l]});
+    }
+    for (auto& s : shp) need += (size_t)s.first * s.second * 9 + s.first;
+    need += (size_t)d->out_ch * d->ch[0] + d->out_ch;
+    if (d->has_bn)
+        for (int l = 0; l < L; ++l) need += 8 * (size_t)d->ch[l];
+    if (n_floats != need) return fail(c, LNR_E_ARG, "weight count does not match the descriptor");
+    for (size_t i = 0; i < n_floats; ++i)
+        if (!std::isfinite(w[i])) return fail(c, LNR_E_ARG, "non-finite weight");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& Lr : c->unet.convs) {
+        if (Lr.w32) cudaFree(Lr.w32);
+        if (Lr.b32) cudaFree(Lr.b32);
+        if (Lr.wtc) cudaFree(Lr.wtc);
+        if (Lr.wscale) cudaFree(Lr.wscale);
+    }
+    Unet u;
+    u.levels = L;
+    for (int l = 0; l < L; ++l) u.ch[l] = d->ch[l];
+    u.in_ch = d->in_ch;
+    u.out_ch = d->out_ch;
+    u.head_w = c->unet.head_w;
+    u.head_b = c->unet.head_b;
+    const float* p = w;
+    for (size_t i = 0; i < shp.size(); ++i) {
+        ConvLayer Lr;
+        const int co = shp[i].first, ci = shp[i].second;
+        Lr.cout = co;
+        const bool enc = i < (size_t)2 * L;
+        Lr.level = enc ? (int)(i / 2) : (int)(L - 2 - (i - 2 * L) / 2);
+        const bool dec_a = !enc && ((i - 2 * L) % 2 == 0);
+        Lr.cin0 = dec_a ? d->ch[Lr.level] : ci;
+        Lr.cin1 = dec_a ? d->ch[Lr.level + 1] : 0;
+        Lr.pool = enc && (i % 2 == 1) && Lr.level < L - 1;
+        Lr.head = (i + 1 == shp.size()) && L > 1;
+        Lr.wf.assign(p, p + (size_t)co * ci * 9);
+        p += (size_t)co * ci * 9;
+        Lr.bf.assign(p, p + co);
+        p += co;
+        u.convs.push_back(std::move(Lr));
+    }
+    u.head_wh.assign(p, p + (size_t)d->out_ch * d->ch[0]);
+    p += (size_t)d->out_ch * d->ch[0];
+    u.head_bh.assign(p, p + d->out_ch);
+    p += d->out_ch;
+    if (d->has_bn) {
+        // fold y = gamma (conv - mean) / sqrt(var + eps) + beta into the encoder convs (FP64)
+        for (int e = 0; e < 2 * L; ++e) {
+            ConvLayer& Lr = u.convs[e];
+            const int co = Lr.cout;
+            const float *g = p, *be = p + co, *mu = p + 2 * co, *var = p + 3 * co;
+            const size_t per = Lr.wf.size() / co;
+            for (int o = 0; o < co; ++o) {
+                const double sc = (double)g[o] / std::sqrt((double)var[o] + kBnEps);
+                for (size_t k = 0; k < per; ++k) Lr.wf[o * per + k] = (float)((double)Lr.wf[o * per + k] * sc);
+                Lr.bf[o] = (float)(((double)Lr.bf[o] - (double)mu[o]) * sc + (double)be[o]);
+            }
+            p += 4 * co;
+        }
+    }
+    c->unet = std::move(u);
+    c->unet_ok = false;
+    lnr_status s = unet_prepare(c);
+    if (s != LNR_OK) return s;
+    c->unet_ok = true;
+    c->prec = prec;
+    c->unet_gen++;
+    if (prec != LNR_FP32 && !tc_available()) {
+        c->prec = LNR_FP32;
+        return fail(c, LNR_E_ARG, "tensor-core precision not available in this build");
+    }
+    return LNR_OK;
+}
+
+lnr_status lnr_set_precision(lnr_ctx* c, lnr_precision prec) {
+    if (!c) return LNR_E_ARG;
+    if (!c->unet_ok) return fail(c, LNR_E_STATE, "set_precision before set_unet");
+    if (prec < LNR_FP32 || prec > LNR_FP8) return fail(c, LNR_E_ARG, "bad precision");
+    if (prec != LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "tensor-core precision not available");
+    c->prec = prec;
+    return LNR_OK;
+}
+
+lnr_status lnr_render_batch(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in, int W, int H,
+                            int nlev, const float* fs, float* out, int on_device) {
+    if (!c) return LNR_E_ARG;
+    lnr_status s = check_frame_args(c, nviews, views, in, W, H, nlev, fs, true);
+    if (s != LNR_OK) return s;
+    if (!out) return fail(c, LNR_E_ARG, "null output");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, nviews, views, in, W, H, nlev, fs);
+    if (s != LNR_OK) return s;
+    enqueue_frame(c, ws, ws.stream, -1, c->prec, c->timing);
+    return finish_output(c, ws, out, (size_t)nviews * W * H * 3, on_device);
+}
+
+lnr_status lnr_render(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev, float fs,
+                      float* out, int on_device) {
+    return lnr_render_batch(c, 1, view, in, W, H, nlev, &fs, out, on_device);
+}
+
+lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev,
+                            float fs, int stage, void* out, int on_device) {
+    if (!c) return LNR_E_ARG;
+    if (stage < LNR_STAGE_KEYS || stage > LNR_STAGE_CULL) return fail(c, LNR_E_ARG, "bad stage");
+    lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, false);
+    if (s != LNR_OK) return s;
+    if (!out) return fail(c, LNR_E_ARG, "null output");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    if (s != LNR_OK) return s;
+    enqueue_frame(c, ws, ws.stream, stage, c->prec, false);
+    const size_t P = (size_t)W * H;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    std::vector<uint8_t> tmp;
+    switch (stage) {
+        case LNR_STAGE_CULL: {
+            uint32_t t[2];
+            e = cudaMemcpyAsync(t, ws.vis_tot.p, 8, cudaMemcpyDeviceToHost, ws.stream);
+            if (!e) e = cudaStreamSynchronize(ws.stream);
+            uint64_t r[2] = {t[0], t[1]};
+            if (!e) e = cudaMemcpy(out, r, 16, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+            break;
+        }
+        case LNR_STAGE_KEYS:
+            e = cudaMemcpyAsync(out, ws.keys.p, 8 * P, kind, ws.stream);
+            break;
+        case LNR_STAGE_RGBDA_RAW: {
+            std::vector<float> d(P);
+            std::vector<uint32_t> col(P);
+            e = cudaMemcpyAsync(d.data(), ws.depth.p, 4 * P, cudaMemcpyDeviceToHost, ws.stream);
+            if (!e) e = cudaMemcpyAsync(col.data(), ws.rgba.p, 4 * P, cudaMemcpyDeviceToHost, ws.stream);
+            if (!e) e = cudaStreamSynchronize(ws.stream);
+            tmp.resize(8 * P);
+            for (size_t q = 0; q < P; ++q) {
+                std::memcpy(&tmp[8 * q], &d[q], 4);
+                std::memcpy(&tmp[8 * q + 4], &col[q], 4);
+            }
+            if (!e) e = cudaMemcpy(out, tmp.data(), 8 * P, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+            break;
+        }
+        case LNR_STAGE_FILTERED:
+            e = cudaMemcpyAsync(out, ws.u0.p, 4 * P, kind, ws.stream);
+            break;
+        case LNR_STAGE_UNET_IN: {
+            DBuf o5;
+            e = o5.ensure(20 * P);
+            if (!e) {
+                launch_unet_in_extract(ws.act[4 * kMaxUnetLevels].p, 0, o5.as<float>(), (int64_t)P, ws.stream);
+                e = cudaMemcpyAsync(out, o5.p, 20 * P, kind, ws.stream);
+                if (!e) e = cudaStreamSynchronize(ws.stream);
+            }
+            o5.release();
+            break;
+        }
+    }
+    if (!e) e = cudaStreamSynchronize(ws.stream);
+    if (!e) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "render_stage");
+    return LNR_OK;
+}
+
+lnr_status lnr_set_timing(lnr_ctx* c, int enable) {
+    if (!c) return LNR_E_ARG;
+    c->timing = enable != 0;
+    return LNR_OK;
+}
+
+lnr_status lnr_get_timing(lnr_ctx* c, double out[8]) {
+    if (!c || !out) return LNR_E_ARG;
+    std::memcpy(out, c->times, sizeof(c->times));
+    return LNR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Internal declarations shared by the CUDA translation units of liblnr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lnr.h"
+
+namespace lnr {
+
+constexpr int kMaxLevels = 6;      // filter pyramid depth handled by the 64x64 tile kernel
+constexpr int kPyrTile = 64;       // resolve + min-pool tile side
+constexpr int kMaxUnetLevels = 8;
+
+// Parameters of one view on the device (filled by the host in FP64, then rounded once).
+struct ViewDev {
+    int32_t anchor[3];
+    float d0[3];
+    float s[9];      // s[3k + r]: component r of grid step k in camera space
+    float Rf[9];     // world->camera rotation, row-major, FP32
+    float fx, fy, cx, cy, znear, zfar;
+    float S;         // keep scale 1 + fs * KEEP_REL
+    float inv_pad;
+};
+
+// One convolution as the GPU runs it.
+struct ConvLayer {
+    int cin0 = 0;       // channels read from the same-resolution source
+    int cin1 = 0;       // channels read from the half-resolution source (nearest 2x up)
+    int cin_pad = 0;    // cin0 + cin1 rounded up to the kernel's K granularity
+    int cout = 0;
+    int level = 0;
+    bool pool = false;  // also write the 2x2 max-pooled output (encoder convs below the bottom)
+    bool head = false;  // fuse the 1x1 head + sigmoid (last decoder conv)
+    float* w32 = nullptr;   // device, FP32 [tap][cin_pad][cout]
+    float* b32 = nullptr;   // device, FP32 [cout]
+    void* wtc = nullptr;    // device, tensor-core weights [cout][tap][cin_pad] (bf16 or fp8)
+    float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null
+    std::vector<float> wf;  // host FP32 OIHW after batch-norm folding
+    std::vector<float> bf;
+};
+
+struct Unet {
+    int levels = 0;
+    int ch[kMaxUnetLevels] = {0};
+    int in_ch = 5, out_ch = 3;
+    std::vector<ConvLayer> convs;   // network order
+    float* head_w = nullptr;        // device FP32 [out_ch][ch0]
+    float* head_b = nullptr;
+    std::vector<float> head_wh, head_bh;
+    std::vector<float> act_scale;   // per conv: FP8 activation scale of its input
+};
+
+// Grow-only device buffer.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Per-launch workspace: everything one batch of views needs on the device.
+struct Workspace {
+    int B = 0, W = 0, H = 0, nlev = 0;
+    DBuf view;                              // ViewDev[B]
+    DBuf cull_flag, cull_cnt, cull_bsum;    // per-cell temporaries
+    DBuf vis_cell, vis_pref, vis_tot;       // compacted visible cells, point prefix, totals
+    DBuf keys;                              // uint64 [B][P]
+    bool keys_dirty = true;
+    DBuf depth, rgba;                       // float / uint32 [B][P]
+    DBuf pyr_m, pyr_u;                      // min-pooled and upsampled levels (all levels)
+    DBuf u0;                                // float [B][P] kept depth (stage tap)
+    DBuf act[4 * kMaxUnetLevels + 2];       // U-Net activations; [4 * kMaxUnetLevels] = U-Net input
+    DBuf out;                               // float [B][P][3]
+    DBuf pinned_view;                       // host pinned ViewDev[B]
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[16] = {nullptr};
+    // CUDA graph of the whole frame for (B, W, H, nlev, precision)
+    cudaGraphExec_t graph = nullptr;
+    int g_B = -1, g_W = -1, g_H = -1, g_nlev = -1, g_prec = -1;
+    uint64_t g_cloud_gen = 0, g_unet_gen = 0;
+    std::vector<std::string> stage_names;
+    void release();
+};
+
+struct Request {
+    uint64_t ticket;
+    lnr_view view;
+    lnr_intrinsics intr;
+    int W, H, nlev;
+    float fs;
+    double t_submit;
+    double t_done = 0.0;
+    bool done = false;
+    std::vector<float> out;
+    size_t act_bytes = 0;
+};
+
+struct Server;
+
+}  // namespace lnr
+
+struct lnr_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // cloud
+    uint64_t n = 0;
+    lnr::DBuf xyz, rgb, scan;
+    uint64_t cloud_gen = 0;
+    // grid
+    bool grid_ok = false;
+    double cell = 0.0;
+    double g0[3] = {0, 0, 0};
+    int32_t dims[3] = {0, 0, 0};
+    int64_t ncells = 0;
+    lnr::DBuf cell_start, ox, oy, oz, rgbs;
+    // U-Net
+    bool unet_ok = false;
+    lnr::Unet unet;
+    lnr_precision prec = LNR_FP32;
+    uint64_t unet_gen = 0;
+    // per-frame workspace of the synchronous calls
+    lnr::Workspace ws;
+    bool timing = false;
+    double times[8] = {0};
+    // serving
+    lnr::Server* server = nullptr;  // owned; deleted by lnr_serve_stop
+    size_t mem_budget = 0;
+};
+
+namespace lnr {
+
+double now_s();
+lnr_status fail(lnr_ctx* c, lnr_status s, const std::string& msg);
+lnr_status cuda_fail(lnr_ctx* c, cudaError_t e, const char* where);
+
+// grid.cu
+cudaError_t grid_bbox(const double* xyz, uint64_t n, double* d_tmp, double out_lohi[6], cudaStream_t st);
+cudaError_t grid_build(lnr_ctx* c, cudaStream_t st);
+
+// raster.cu
+int cull_blocks(int64_t ncells);
+void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+void launch_clear_keys(Workspace& ws, cudaStream_t st);
+void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+// Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
+// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC8, 2 = none (stage taps only).
+void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,
+                     bool write_u0, cudaStream_t st);
+size_t pyramid_floats(int W, int H, int nlev);
+size_t pyramid_offset(int W, int H, int l);
+void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t npx, cudaStream_t st);
+
+// unet.cu
+size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p);
+lnr_status unet_prepare(lnr_ctx* c);
+void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
+                  cudaStream_t st, cudaEvent_t* layer_ev);
+int unet_in_kind(lnr_precision p);
+
+// conv_tc.cu
+bool tc_available();
+cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p);
+void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out,
+             void* pool_out, const float* head_w, const float* head_b, float* head_out, int B,
+             int W, int H, cudaStream_t st);
+
+}  // namespace lnr

@@ -1,0 +1,591 @@
+// Per-frame projection and depth filter of the render path:
+//   cull     frustum culling of grid cells and compaction of the visible ones
+//            (Sec. 1; Sec. 3, "Point Cloud Projection"; Fig. 1)
+//   splat    1x1-pixel projection of the visible cells' points into a 64-bit z-buffer
+//            keyed by (float bits of z << 32 | sorted position)        (Sec. 3)
+//   resolve  keys -> depth D, colour and fill mask A, fused with the whole min-pool
+//            pyramid of a 64x64 tile                                   (Fig. 1; Fig. 2)
+//   upsample one Laplacian-edge-aware upsampling step per level, with the
+//            linear-interpolation fill on non-final levels and, on the final level, the
+//            packing of the U-Net's RGBDA input                        (Fig. 2; Sec. 3)
+//
+// Compiled with --fmad=false and written with explicit round-to-nearest intrinsics: the
+// arithmetic of culling, projection and filtering is exactly the sequence of FP32
+// operations of the method's definition, so the results are bit-exact against any
+// implementation of that same sequence.
+#include <cuda_bf16.h>
+
+#include "lnr_internal.h"
+
+namespace lnr {
+
+void scan_exclusive_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t st);
+
+namespace {
+
+constexpr float kEdgeRel = 0.1f;         // edge when |Laplacian| > kEdgeRel * depth
+constexpr float kCullPad = 1.0f / 64.0f; // cells grow by 1/64 of a step on every side
+constexpr int kCullThreads = 256;
+constexpr int kCullPer = 4;
+constexpr int kCullTile = kCullThreads * kCullPer;
+constexpr int kSplatThreads = 256;
+constexpr int kSplatChunk = 2048;
+constexpr uint64_t kEmpty = ~0ull;
+
+__device__ __forceinline__ void cell_cam(int64_t i, int64_t j, int64_t k, const ViewDev& v, float o[3]) {
+    float di = (float)(i - v.anchor[0]), dj = (float)(j - v.anchor[1]), dk = (float)(k - v.anchor[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float t = __fmaf_rn(di, v.s[0 + r], v.d0[r]);
+        t = __fmaf_rn(dj, v.s[3 + r], t);
+        o[r] = __fmaf_rn(dk, v.s[6 + r], t);
+    }
+}
+
+// ---------------------------------------------------------------- culling ----
+
+__device__ bool cell_visible(int64_t i, int64_t j, int64_t k, const ViewDev& v, int W, int H) {
+    float o[3];
+    cell_cam(i, j, k, v, o);
+    const float cxw = __fsub_rn(v.cx, (float)W), cyh = __fsub_rn(v.cy, (float)H);
+    bool out_all[6] = {true, true, true, true, true, true};
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        float tx = (corner & 1) ? 1.0f + kCullPad : -kCullPad;
+        float ty = (corner & 2) ? 1.0f + kCullPad : -kCullPad;
+        float tz = (corner & 4) ? 1.0f + kCullPad : -kCullPad;
+        float p[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            float t = __fmaf_rn(tx, v.s[0 + r], o[r]);
+            t = __fmaf_rn(ty, v.s[3 + r], t);
+            p[r] = __fmaf_rn(tz, v.s[6 + r], t);
+        }
+        const float x = p[0], y = p[1], z = p[2];
+        float pl[6];
+        pl[0] = __fsub_rn(z, v.znear);
+        pl[1] = __fsub_rn(v.zfar, z);
+        pl[2] = __fmaf_rn(v.fx, x, __fmul_rn(v.cx, z));
+        pl[3] = -__fmaf_rn(v.fx, x, __fmul_rn(cxw, z));
+        pl[4] = __fmaf_rn(v.fy, y, __fmul_rn(v.cy, z));
+        pl[5] = -__fmaf_rn(v.fy, y, __fmul_rn(cyh, z));
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out_all[q] = out_all[q] && (pl[q] < 0.0f);
+    }
+    bool culled = false;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) culled |= out_all[q];
+    return !culled;
+}
+
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb,
+                                            uint32_t& ta, uint32_t& tb) {
+    __shared__ uint32_t wa[kCullThreads / 32], wb[kCullThreads / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t xa = a, xb = b;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) { xa += ya; xb += yb; }
+    }
+    if (lane == 31) { wa[warp] = xa; wb[warp] = xb; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = kCullThreads / 32;
+        uint32_t sa = lane < nw ? wa[lane] : 0, sb = lane < nw ? wb[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) { sa += ya; sb += yb; }
+        }
+        if (lane < nw) { wa[lane] = sa; wb[lane] = sb; }
+    }
+    __syncthreads();
+    ea = (warp ? wa[warp - 1] : 0) + xa - a;
+    eb = (warp ? wb[warp - 1] : 0) + xb - b;
+    ta = wa[kCullThreads / 32 - 1];
+    tb = wb[kCullThreads / 32 - 1];
+    __syncthreads();
+}
+
+// Phase 1: visibility of every cell, block-local ranks of the visible non-empty cells and
+// of their points.  flag[c] = local rank or ~0; cnt[c] = local point prefix.
+__global__ void __launch_bounds__(kCullThreads) k_cull_block(
+    const ViewDev* __restrict__ views, const uint32_t* __restrict__ cell_start, int dx, int dy,
+    int dz, int64_t C, int W, int H, uint32_t* __restrict__ flag, uint32_t* __restrict__ cnt,
+    uint32_t* __restrict__ bsum, int nb) {
+    const int view = blockIdx.y;
+    const ViewDev v = views[view];
+    int64_t c0 = (int64_t)blockIdx.x * kCullTile + (int64_t)threadIdx.x * kCullPer;
+    uint32_t f[kCullPer], n[kCullPer], sf = 0, sn = 0;
+#pragma unroll
+    for (int e = 0; e < kCullPer; ++e) {
+        int64_t c = c0 + e;
+        f[e] = 0;
+        n[e] = 0;
+        if (c < C) {
+            uint32_t cntc = cell_start[c + 1] - cell_start[c];
+            if (cntc) {
+                int64_t i = c % dx, j = (c / dx) % dy, k = c / ((int64_t)dx * dy);
+                if (cell_visible(i, j, k, v, W, H)) {
+                    f[e] = 1;
+                    n[e] = cntc;
+                }
+            }
+        }
+        sf += f[e];
+        sn += n[e];
+    }
+    uint32_t ef, en, tf, tn;
+    block_scan2(sf, sn, ef, en, tf, tn);
+    uint32_t* fl = flag + (size_t)view * C;
+    uint32_t* ct = cnt + (size_t)view * C;
+#pragma unroll
+    for (int e = 0; e < kCullPer; ++e) {
+        int64_t c = c0 + e;
+        if (c < C) {
+            fl[c] = f[e] ? ef : ~0u;
+            ct[c] = en;
+        }
+        ef += f[e];
+        en += n[e];
+    }
+    if (threadIdx.x == 0) {
+        bsum[((size_t)view * nb + blockIdx.x) * 2 + 0] = tf;
+        bsum[((size_t)view * nb + blockIdx.x) * 2 + 1] = tn;
+    }
+}
+
+// Phase 2: one block per view scans the block sums in place and writes the totals
+// tot[view] = {visible non-empty cells, visible points}.
+__global__ void __launch_bounds__(kCullThreads) k_cull_scan(uint32_t* __restrict__ bsum, int nb,
+                                                            uint32_t* __restrict__ tot) {
+    const int view = blockIdx.x;
+    uint32_t* bs = bsum + (size_t)view * nb * 2;
+    uint32_t carry_a = 0, carry_b = 0;
+    for (int base = 0; base < nb; base += kCullThreads) {
+        int b = base + threadIdx.x;
+        uint32_t a = b < nb ? bs[2 * b] : 0, p = b < nb ? bs[2 * b + 1] : 0;
+        uint32_t ea, eb, ta, tb;
+        block_scan2(a, p, ea, eb, ta, tb);
+        if (b < nb) {
+            bs[2 * b] = carry_a + ea;
+            bs[2 * b + 1] = carry_b + eb;
+        }
+        carry_a += ta;
+        carry_b += tb;
+    }
+    if (threadIdx.x == 0) {
+        tot[2 * view] = carry_a;
+        tot[2 * view + 1] = carry_b;
+    }
+}
+
+// Phase 3: compaction.  vis_cell[view][r] = cell id, vis_pref[view][r] = visible points
+// before it.
+__global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ cnt,
+                               const uint32_t* __restrict__ bsum, int nb, int64_t C,
+                               uint32_t* __restrict__ vis_cell, uint32_t* __restrict__ vis_pref) {
+    const int view = blockIdx.y;
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    uint32_t f = flag[(size_t)view * C + c];
+    if (f == ~0u) return;
+    int b = (int)(c / kCullTile);
+    const uint32_t* bs = bsum + ((size_t)view * nb + b) * 2;
+    uint32_t r = bs[0] + f;
+    vis_cell[(size_t)view * C + r] = (uint32_t)c;
+    vis_pref[(size_t)view * C + r] = bs[1] + cnt[(size_t)view * C + c];
+}
+
+// ------------------------------------------------------------------ splat ----
+
+struct __align__(16) ChunkCell {
+    float o[3];      // camera-space origin of the cell
+    uint32_t pref;   // visible points before the cell
+    uint32_t base;   // sorted position of its first point minus pref (mod 2^32)
+};
+
+__global__ void __launch_bounds__(kSplatThreads) k_splat(
+    const ViewDev* __restrict__ views, const uint32_t* __restrict__ cell_start, int dx, int dy,
+    int64_t C, const uint32_t* __restrict__ vis_cell, const uint32_t* __restrict__ vis_pref,
+    const uint32_t* __restrict__ tot, const float* __restrict__ ox, const float* __restrict__ oy,
+    const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys) {
+    __shared__ ChunkCell cells[kSplatChunk];
+    __shared__ int s_vc0, s_nc;
+    const int view = blockIdx.y;
+    const ViewDev v = views[view];
+    const uint32_t nvc = tot[2 * view], npts = tot[2 * view + 1];
+    const uint32_t* vc = vis_cell + (size_t)view * C;
+    const uint32_t* vp = vis_pref + (size_t)view * C;
+    unsigned long long* kv = keys + (size_t)view * W * H;
+    const float Wf = (float)W, Hf = (float)H;
+    for (uint64_t chunk = blockIdx.x;; chunk += gridDim.x) {
+        uint64_t start = chunk * kSplatChunk;
+        if (start >= npts) break;
+        uint32_t end = (uint32_t)(start + kSplatChunk < (uint64_t)npts ? start + kSplatChunk : (uint64_t)npts);
+        if (threadIdx.x == 0) {
+            // last visible cell with pref <= start, and last with pref < end
+            uint32_t lo = 0, hi = nvc - 1;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (vp[mid] <= (uint32_t)start) lo = mid; else hi = mid - 1;
+            }
+            uint32_t a = lo;
+            hi = nvc - 1;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (vp[mid] < end) lo = mid; else hi = mid - 1;
+            }
+            s_vc0 = (int)a;
+            s_nc = (int)(lo - a + 1);
+        }
+        __syncthreads();
+        const int vc0 = s_vc0, nc = s_nc;
+        for (int t = threadIdx.x; t < nc; t += kSplatThreads) {
+            uint32_t c = vc[vc0 + t];
+            int64_t i = c % (uint32_t)dx, j = (c / (uint32_t)dx) % (uint32_t)dy, k = c / ((uint32_t)dx * (uint32_t)dy);
+            ChunkCell cc;
+            cell_cam(i, j, k, v, cc.o);
+            cc.pref = vp[vc0 + t];
+            cc.base = cell_start[c] - cc.pref;
+            cells[t] = cc;
+        }
+        __syncthreads();
+        int cur = 0;
+        for (uint32_t e = (uint32_t)start + threadIdx.x; e < end; e += kSplatThreads) {
+            // the cell of element e: last chunk cell with pref <= e (elements increase)
+            int lo = cur, hi = nc - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (cells[mid].pref <= e) lo = mid; else hi = mid - 1;
+            }
+            cur = lo;
+            const ChunkCell& cc = cells[lo];
+            uint32_t pos = e + cc.base;
+            float px = ox[pos], py = oy[pos], pz = oz[pos];
+            float p[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                float t = __fmaf_rn(v.Rf[3 * r + 2], pz, cc.o[r]);
+                t = __fmaf_rn(v.Rf[3 * r + 1], py, t);
+                p[r] = __fmaf_rn(v.Rf[3 * r + 0], px, t);
+            }
+            const float z = p[2];
+            if (!(z > v.znear && z < v.zfar)) continue;
+            const float u = __fadd_rn(__fdiv_rn(__fmul_rn(v.fx, p[0]), z), v.cx);
+            const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
+            if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
+            const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos;
+            atomicMin(&kv[pix], key);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_fill_u64(unsigned long long* __restrict__ p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = kEmpty;
+}
+
+// --------------------------------------------------- resolve + min-pool pyramid ----
+
+// One 64x64 tile: keys -> depth (+inf empty) and rgba (r | g<<8 | b<<16 | A<<24), keys
+// reset to empty for the next frame, then every min-pool level of the tile (kernel 2x2,
+// stride 2; level sizes ceil(W/2^l) x ceil(H/2^l); pixels outside the image count as
+// +inf, so each level pixel is the minimum over its clipped 2^l x 2^l block).
+__global__ void __launch_bounds__(256) k_resolve_pyramid(
+    unsigned long long* __restrict__ keys, const uint32_t* __restrict__ rgbs, int W, int H, int nlev,
+    float* __restrict__ depth, uint32_t* __restrict__ rgba, float* __restrict__ pyr, size_t pyr_stride) {
+    __shared__ float s[64][65];
+    __shared__ float t[32][33];
+    const int view = blockIdx.z;
+    const size_t P = (size_t)W * H;
+    unsigned long long* kv = keys + view * P;
+    float* dv = depth + view * P;
+    uint32_t* cv = rgba + view * P;
+    const int x = threadIdx.x & 63, y0 = threadIdx.x >> 6;
+    const int gx = blockIdx.x * 64 + x;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+        const int y = y0 + 4 * i;
+        const int gy = blockIdx.y * 64 + y;
+        float d = INFINITY;
+        if (gx < W && gy < H) {
+            const size_t q = (size_t)gy * W + gx;
+            const unsigned long long key = kv[q];
+            uint32_t col = 0;
+            if (key != kEmpty) {
+                d = __uint_as_float((uint32_t)(key >> 32));
+                col = (rgbs[(uint32_t)key] & 0x00ffffffu) | (1u << 24);
+                kv[q] = kEmpty;
+            }
+            dv[q] = d;
+            cv[q] = col;
+        }
+        s[y][x] = d;
+    }
+    __syncthreads();
+    float* lev = pyr + view * pyr_stride;
+    int Wl = W, Hl = H;
+    for (int l = 1; l <= nlev; ++l) {
+        const int T = 64 >> l;                  // tile side at this level
+        Wl = (Wl + 1) >> 1;
+        Hl = (Hl + 1) >> 1;
+        // read level l-1 from s (l odd) or t (l even), write level l into the other
+        for (int idx = threadIdx.x; idx < T * T; idx += 256) {
+            const int lx = idx % T, ly = idx / T;
+            float m;
+            if (l & 1) {
+                m = fminf(fminf(s[2 * ly][2 * lx], s[2 * ly][2 * lx + 1]),
+                          fminf(s[2 * ly + 1][2 * lx], s[2 * ly + 1][2 * lx + 1]));
+                t[ly][lx] = m;
+            } else {
+                m = fminf(fminf(t[2 * ly][2 * lx], t[2 * ly][2 * lx + 1]),
+                          fminf(t[2 * ly + 1][2 * lx], t[2 * ly + 1][2 * lx + 1]));
+                s[ly][lx] = m;
+            }
+            const int ox_ = blockIdx.x * T + lx, oy_ = blockIdx.y * T + ly;
+            if (ox_ < Wl && oy_ < Hl) lev[(size_t)oy_ * Wl + ox_] = m;
+        }
+        lev += (size_t)Wl * Hl;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ upsample ----
+
+struct UpArgs {
+    const ViewDev* views;
+    const float* Mf;     // fine min-pooled level (level 0: the depth image)
+    const float* Mc;     // coarse min-pooled level
+    const float* Uc;     // coarse upsampled level (the coarsest: Mc itself)
+    float* Uf;           // fine upsampled level (levels > 0)
+    size_t f_stride, c_stride, uc_stride, uf_stride;  // per-view strides (floats)
+    int Wf, Hf, Wc, Hc;
+    int fill;            // non-final level: fill empty pixels by interpolation
+    // final level only
+    const uint32_t* rgba;
+    void* unet_in;       // NHWC, 8 channels
+    int kind;            // 0 = FP32, 1 = BF16, 2 = none
+    float* u0;           // kept depth tap (nullable)
+};
+
+__device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, float r, float g, float b,
+                                              float d, float a) {
+    if (kind == 0) {
+        float4* p = reinterpret_cast<float4*>(static_cast<float*>(base) + q * 8);
+        p[0] = make_float4(r, g, b, d);
+        p[1] = make_float4(a, 0.f, 0.f, 0.f);
+    } else if (kind == 1) {
+        __nv_bfloat162 v0 = __floats2bfloat162_rn(r, g), v1 = __floats2bfloat162_rn(b, d);
+        __nv_bfloat162 v2 = __floats2bfloat162_rn(a, 0.f), v3 = __floats2bfloat162_rn(0.f, 0.f);
+        uint4 u;
+        u.x = *reinterpret_cast<uint32_t*>(&v0);
+        u.y = *reinterpret_cast<uint32_t*>(&v1);
+        u.z = *reinterpret_cast<uint32_t*>(&v2);
+        u.w = *reinterpret_cast<uint32_t*>(&v3);
+        reinterpret_cast<uint4*>(base)[q] = u;
+    }
+}
+
+__device__ __forceinline__ void pack_pixel(const UpArgs& a, const ViewDev& v, int view, size_t q, bool keep, float m) {
+    const size_t P = (size_t)a.Wf * a.Hf;
+    if (a.u0) a.u0[view * P + q] = keep ? m : INFINITY;
+    if (a.kind == 2) return;
+    if (keep) {
+        const uint32_t c = a.rgba[view * P + q];
+        store_unet_in(a.unet_in, a.kind, view * P + q, __fdiv_rn((float)(c & 255u), 255.0f),
+                      __fdiv_rn((float)((c >> 8) & 255u), 255.0f), __fdiv_rn((float)((c >> 16) & 255u), 255.0f),
+                      __fdiv_rn(m, v.zfar), 1.0f);
+    } else {
+        store_unet_in(a.unet_in, a.kind, view * P + q, 0.f, 0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// One thread per coarse pixel p of a 32x8 tile; the coarse levels are staged with a
+// one-pixel clamped halo, so replicated borders come for free.
+__global__ void __launch_bounds__(256) k_upsample(const UpArgs a) {
+    __shared__ float sM[10][34], sU[10][34];
+    const int view = blockIdx.z;
+    const ViewDev v = a.views[view];
+    const float* Mc = a.Mc + view * a.c_stride;
+    const float* Uc = a.Uc + view * a.uc_stride;
+    const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 8;
+    for (int idx = threadIdx.x; idx < 340; idx += 256) {
+        const int hx = idx % 34, hy = idx / 34;
+        const int gx = min(max(tx0 + hx - 1, 0), a.Wc - 1), gy = min(max(ty0 + hy - 1, 0), a.Hc - 1);
+        sM[hy][hx] = Mc[(size_t)gy * a.Wc + gx];
+        sU[hy][hx] = Uc[(size_t)gy * a.Wc + gx];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int cx = tx0 + lx, cy = ty0 + ly;
+    if (cx >= a.Wc || cy >= a.Hc) return;
+    const int sx = lx + 1, sy = ly + 1;
+    const float d = sM[sy][sx];
+    bool edge = false;
+    if (d != INFINITY) {
+        const float nb[4] = {sM[sy][sx - 1], sM[sy][sx + 1], sM[sy - 1][sx], sM[sy + 1][sx]};
+        float te[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) te[e] = nb[e] == INFINITY ? 0.0f : __fsub_rn(nb[e], d);
+        const float lap = __fadd_rn(__fadd_rn(te[0], te[1]), __fadd_rn(te[2], te[3]));
+        edge = fabsf(lap) > __fmul_rn(kEdgeRel, d);
+    }
+    float ref;
+    if (edge) {
+        ref = INFINITY;
+#pragma unroll
+        for (int b = -1; b <= 1; ++b)
+#pragma unroll
+            for (int c = -1; c <= 1; ++c) ref = fminf(ref, sU[sy + b][sx + c]);
+    } else {
+        ref = sU[sy][sx];
+    }
+    const float thr = __fmul_rn(ref, v.S);
+    const float* Mf = a.Mf + view * a.f_stride;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int fx = 2 * cx + c, fy = 2 * cy + b;
+            if (fx >= a.Wf || fy >= a.Hf) continue;
+            const size_t q = (size_t)fy * a.Wf + fx;
+            const float m = Mf[q];
+            const bool keep = (m <= thr) && (m != INFINITY);
+            if (a.Uf) {
+                float val = keep ? m : INFINITY;
+                if (!keep && a.fill) {
+                    const int fxs = c ? sx + 1 : sx - 1;   // far tap in x (clamped by the halo)
+                    const int fys = b ? sy + 1 : sy - 1;
+                    const float tap[4] = {sU[sy][sx], sU[sy][fxs], sU[fys][sx], sU[fys][fxs]};
+                    const float wt[4] = {0.5625f, 0.1875f, 0.1875f, 0.0625f};
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (tap[e] == INFINITY) continue;
+                        num = __fadd_rn(num, __fmul_rn(wt[e], tap[e]));
+                        den = __fadd_rn(den, wt[e]);
+                    }
+                    if (den > 0.0f) val = __fdiv_rn(num, den);
+                }
+                a.Uf[view * a.uf_stride + q] = val;
+            } else {
+                pack_pixel(a, v, view, q, keep, m);
+            }
+        }
+}
+
+// n_levels = 0: no filter, every filled pixel is kept.
+__global__ void k_pack_direct(const UpArgs a, int B) {
+    const size_t P = (size_t)a.Wf * a.Hf;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * B; i += (size_t)gridDim.x * blockDim.x) {
+        const int view = (int)(i / P);
+        const size_t q = i % P;
+        const float m = a.Mf[view * a.f_stride + q];
+        pack_pixel(a, a.views[view], view, q, m != INFINITY, m);
+    }
+}
+
+__global__ void k_extract5(const void* in, int kind, float* out, int64_t npx) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npx) return;
+    for (int c = 0; c < 5; ++c) {
+        float v;
+        if (kind == 0) v = static_cast<const float*>(in)[q * 8 + c];
+        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 8 + c]);
+        out[q * 5 + c] = v;
+    }
+}
+
+}  // namespace
+
+int cull_blocks(int64_t ncells) { return (int)((ncells + kCullTile - 1) / kCullTile); }
+
+void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
+    const int nb = cull_blocks(c->ncells);
+    dim3 g1(nb, ws.B);
+    k_cull_block<<<g1, kCullThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
+                                              c->dims[1], c->dims[2], c->ncells, ws.W, ws.H,
+                                              ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
+                                              ws.cull_bsum.as<uint32_t>(), nb);
+    k_cull_scan<<<ws.B, kCullThreads, 0, st>>>(ws.cull_bsum.as<uint32_t>(), nb, ws.vis_tot.as<uint32_t>());
+    dim3 g3((unsigned)((c->ncells + 255) / 256), ws.B);
+    k_cull_compact<<<g3, 256, 0, st>>>(ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
+                                       ws.cull_bsum.as<uint32_t>(), nb, c->ncells, ws.vis_cell.as<uint32_t>(),
+                                       ws.vis_pref.as<uint32_t>());
+}
+
+void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
+    int per_view = std::max(1, (c->num_sms * 8) / ws.B);
+    dim3 g(per_view, ws.B);
+    k_splat<<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
+                                         c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
+                                         ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(), c->ox.as<float>(),
+                                         c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
+                                         ws.keys.as<unsigned long long>());
+}
+
+void launch_clear_keys(Workspace& ws, cudaStream_t st) {
+    // the whole allocation: a tap that stopped after the splat may have left keys of an
+    // earlier, larger frame behind
+    size_t n = ws.keys.bytes / 8;
+    k_fill_u64<<<1024, 256, 0, st>>>(ws.keys.as<unsigned long long>(), n);
+    ws.keys_dirty = false;
+}
+
+size_t pyramid_offset(int W, int H, int l) {
+    size_t off = 0;
+    for (int k = 1; k < l; ++k) {
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+        off += (size_t)W * H;
+    }
+    return off;
+}
+size_t pyramid_floats(int W, int H, int nlev) { return pyramid_offset(W, H, nlev + 1) + 1; }
+
+void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
+    dim3 g((ws.W + 63) / 64, (ws.H + 63) / 64, ws.B);
+    k_resolve_pyramid<<<g, 256, 0, st>>>(ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(), ws.W, ws.H,
+                                         ws.nlev, ws.depth.as<float>(), ws.rgba.as<uint32_t>(), ws.pyr_m.as<float>(),
+                                         pyramid_floats(ws.W, ws.H, ws.nlev));
+}
+
+void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int kind, bool write_u0,
+                     cudaStream_t st) {
+    (void)c;
+    const size_t P = (size_t)ws.W * ws.H;
+    const size_t pstride = pyramid_floats(ws.W, ws.H, ws.nlev);
+    UpArgs a{};
+    a.views = ws.view.as<ViewDev>();
+    a.rgba = ws.rgba.as<uint32_t>();
+    a.unet_in = unet_in;
+    a.kind = kind;
+    a.u0 = write_u0 ? ws.u0.as<float>() : nullptr;
+    int Wl = ws.W, Hl = ws.H;
+    for (int k = 0; k < l; ++k) { Wl = (Wl + 1) / 2; Hl = (Hl + 1) / 2; }
+    a.Wf = Wl; a.Hf = Hl;
+    a.Wc = (Wl + 1) / 2; a.Hc = (Hl + 1) / 2;
+    if (ws.nlev == 0) {
+        a.Mf = ws.depth.as<float>();
+        a.f_stride = P;
+        k_pack_direct<<<2048, 256, 0, st>>>(a, ws.B);
+        return;
+    }
+    if (l == 0) { a.Mf = ws.depth.as<float>(); a.f_stride = P; }
+    else { a.Mf = ws.pyr_m.as<float>() + pyramid_offset(ws.W, ws.H, l); a.f_stride = pstride; }
+    a.Mc = ws.pyr_m.as<float>() + pyramid_offset(ws.W, ws.H, l + 1);
+    a.c_stride = pstride;
+    if (l + 1 == ws.nlev) { a.Uc = a.Mc; a.uc_stride = pstride; }
+    else { a.Uc = ws.pyr_u.as<float>() + pyramid_offset(ws.W, ws.H, l + 1); a.uc_stride = pstride; }
+    if (l > 0) { a.Uf = ws.pyr_u.as<float>() + pyramid_offset(ws.W, ws.H, l); a.uf_stride = pstride; a.fill = 1; }
+    dim3 g((a.Wc + 31) / 32, (a.Hc + 7) / 8, ws.B);
+    k_upsample<<<g, 256, 0, st>>>(a);
+}
+
+void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t npx, cudaStream_t st) {
+    k_extract5<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(unet_in, kind, out5, npx);
+}
+
+}  // namespace lnr

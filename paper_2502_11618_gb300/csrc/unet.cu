@@ -1,0 +1,289 @@
+// U-Net reconstruction (Fig. 1; Sec. 3, "U-Net Reconstruction"): encoder of two 3x3
+// convolutions + ReLU per level with 2x2 max pooling between levels, decoder of nearest
+// 2x upsampling, concatenation [skip, upsampled] and two 3x3 convolutions + ReLU, then a
+// 1x1 head with a sigmoid.  Batch norm after the encoder convolutions is folded into them
+// when the weights are loaded.
+//
+// This file holds the FP32 path (CUDA-core implicit GEMM; the accuracy reference of the
+// GPU) and the layer orchestration shared by every precision.  Pooling, upsampling and
+// concatenation are fused into the convolutions: nothing but conv outputs is written.
+#include <cmath>
+
+#include "lnr_internal.h"
+
+namespace lnr {
+namespace {
+
+struct ConvArgsF32 {
+    const float* src0;  // NHWC, c0 channels, output resolution
+    const float* src1;  // NHWC, c1 channels, half resolution (read nearest-upsampled), or null
+    int c0, c1;
+    int W, H;
+    const float* w;     // [9][c0 + c1][cout]
+    const float* bias;  // [cout]
+    int cout;
+    float* out;         // NHWC, cout channels
+    float* pool_out;    // NHWC, cout channels at W/2 x H/2, or null
+};
+
+// Tile: 2 rows x TW pixels x CT output channels.  Thread = one 2x2 pixel quad x 8 output
+// channels; K is walked 8 input channels at a time, all 9 taps per chunk, from a shared
+// halo tile of 4 rows x (TW+2) pixels.
+template <int TW, int CT>
+__global__ void __launch_bounds__(256) k_conv3x3_f32(const ConvArgsF32 a) {
+    constexpr int NCOG = CT / 8;
+    constexpr int HW = TW + 2;
+    static_assert((TW / 2) * NCOG == 256, "256 threads");
+    __shared__ float sin_[8][4][HW];
+    __shared__ __align__(16) float sw[9][8][CT];
+    const int cog = threadIdx.x % NCOG, q = threadIdx.x / NCOG;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * 2;
+    const int nco_blocks = a.cout / CT;
+    const int view = blockIdx.z / nco_blocks;
+    const int co0 = (blockIdx.z % nco_blocks) * CT;
+    const int cin = a.c0 + a.c1;
+    const size_t P = (size_t)a.W * a.H;
+    const int Wh = a.W >> 1, Hh = a.H >> 1;
+    const float* s0 = a.src0 + view * P * a.c0;
+    const float* s1 = a.src1 ? a.src1 + view * (size_t)Wh * Hh * a.c1 : nullptr;
+    float acc[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[p][j] = 0.f;
+
+    for (int cb = 0; cb < cin; cb += 8) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 4 * HW * 2; idx += 256) {
+            const int h = idx & 1, j = (idx >> 1) % HW, r = (idx >> 1) / HW;
+            const int gx = x0 - 1 + j, gy = y0 - 1 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) {
+                if (cb < a.c0)
+                    v = *reinterpret_cast<const float4*>(s0 + ((size_t)gy * a.W + gx) * a.c0 + cb + 4 * h);
+                else
+                    v = *reinterpret_cast<const float4*>(s1 + ((size_t)(gy >> 1) * Wh + (gx >> 1)) * a.c1 +
+                                                         (cb - a.c0) + 4 * h);
+            }
+            sin_[4 * h + 0][r][j] = v.x;
+            sin_[4 * h + 1][r][j] = v.y;
+            sin_[4 * h + 2][r][j] = v.z;
+            sin_[4 * h + 3][r][j] = v.w;
+        }
+        for (int idx = threadIdx.x; idx < 9 * 8 * (CT / 4); idx += 256) {
+            const int c4 = idx % (CT / 4), ci = (idx / (CT / 4)) % 8, t = idx / (CT / 4) / 8;
+            *reinterpret_cast<float4*>(&sw[t][ci][4 * c4]) =
+                *reinterpret_cast<const float4*>(a.w + ((size_t)t * cin + cb + ci) * a.cout + co0 + 4 * c4);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int ci = 0; ci < 8; ++ci) {
+            float in[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) in[r][c] = sin_[ci][r][2 * q + c];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float4 w0 = *reinterpret_cast<const float4*>(&sw[ky * 3 + kx][ci][cog * 8]);
+                    const float4 w1 = *reinterpret_cast<const float4*>(&sw[ky * 3 + kx][ci][cog * 8 + 4]);
+                    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    const float av[4] = {in[ky][kx], in[ky][kx + 1], in[ky + 1][kx], in[ky + 1][kx + 1]};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[p][j] = fmaf(av[p], wv[j], acc[p][j]);
+                }
+        }
+    }
+    const int co = co0 + cog * 8;
+    float b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = a.bias[co + j];
+    float mx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mx[j] = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int x = x0 + 2 * q + (p & 1), y = y0 + (p >> 1);
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            o[j] = fmaxf(acc[p][j] + b[j], 0.f);
+            mx[j] = fmaxf(mx[j], o[j]);
+        }
+        if (x < a.W && y < a.H) {
+            float4* dst = reinterpret_cast<float4*>(a.out + (view * P + (size_t)y * a.W + x) * a.cout + co);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
+    if (a.pool_out) {
+        const int px = (x0 >> 1) + q, py = y0 >> 1;
+        if (px < Wh && py < Hh) {
+            float4* dst = reinterpret_cast<float4*>(a.pool_out + (view * (size_t)Wh * Hh + (size_t)py * Wh + px) * a.cout + co);
+            dst[0] = make_float4(mx[0], mx[1], mx[2], mx[3]);
+            dst[1] = make_float4(mx[4], mx[5], mx[6], mx[7]);
+        }
+    }
+}
+
+// 1x1 head + sigmoid: out[q][o] = 1 / (1 + exp(-(b[o] + sum_c w[o][c] x[q][c]))).
+__global__ void k_head_f32(const float* __restrict__ x, int C, const float* __restrict__ w,
+                           const float* __restrict__ b, int O, float* __restrict__ out, size_t npx) {
+    size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (q >= npx) return;
+    const float* xp = x + q * C;
+    for (int o = 0; o < O; ++o) {
+        float acc = b[o];
+        for (int c = 0; c < C; ++c) acc = fmaf(w[o * C + c], xp[c], acc);
+        out[q * O + o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
+void conv_f32(const ConvLayer& L, const float* src0, const float* src1, float* out, float* pool_out, int B,
+              int W, int H, cudaStream_t st) {
+    ConvArgsF32 a{src0, src1, L.cin0 == 5 ? 8 : L.cin0, L.cin1, W, H, L.w32, L.b32, L.cout, out, pool_out};
+    if (L.cout % 64 == 0) {
+        dim3 g((W + 63) / 64, (H + 1) / 2, B * (L.cout / 64));
+        k_conv3x3_f32<64, 64><<<g, 256, 0, st>>>(a);
+    } else {
+        dim3 g((W + 127) / 128, (H + 1) / 2, B * (L.cout / 32));
+        k_conv3x3_f32<128, 32><<<g, 256, 0, st>>>(a);
+    }
+}
+
+// Activation buffer slots: for level l, 4*l + {0: first conv out, 1: skip, 2: pooled, 3: decoder out}.
+inline int slot(int l, int k) { return 4 * l + k; }
+
+}  // namespace
+
+int unet_in_kind(lnr_precision p) { return p == LNR_FP32 ? 0 : 1; }
+
+static size_t elem_bytes(lnr_precision p) { return p == LNR_FP32 ? 4 : 2; }
+
+size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p) {
+    size_t tot = (size_t)B * W * H * 8 * elem_bytes(p);  // input
+    for (int l = 0; l < u.levels; ++l) {
+        size_t Pl = (size_t)B * (W >> l) * (H >> l);
+        tot += Pl * u.ch[l] * elem_bytes(p) * 4;
+    }
+    tot += (size_t)B * W * H * 3 * 4;  // output
+    return tot;
+}
+
+// Ensure the activation buffers of the workspace for (B, W, H).
+static cudaError_t ensure_acts(const Unet& u, Workspace& ws, lnr_precision p) {
+    const size_t e = elem_bytes(p);
+    cudaError_t err;
+    for (int l = 0; l < u.levels; ++l) {
+        size_t Pl = (size_t)ws.B * (ws.W >> l) * (ws.H >> l);
+        for (int k = 0; k < 4; ++k) {
+            size_t n = (k == 2) ? (size_t)ws.B * (ws.W >> (l + 1)) * (ws.H >> (l + 1)) * u.ch[l] : Pl * u.ch[l];
+            if ((err = ws.act[slot(l, k)].ensure(n * e + 256))) return err;
+        }
+    }
+    return cudaSuccess;
+}
+
+void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
+                  cudaStream_t st, cudaEvent_t* layer_ev) {
+    const Unet& u = c->unet;
+    if (ensure_acts(u, ws, p) != cudaSuccess) return;
+    const int L = u.levels;
+    int ci = 0;
+    const void* x = in;
+    int ev = 0;
+    auto mark = [&]() {
+        if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
+    };
+    mark();
+    for (int l = 0; l < L; ++l) {
+        const int W = ws.W >> l, H = ws.H >> l;
+        void* t = ws.act[slot(l, 0)].p;
+        void* s = ws.act[slot(l, 1)].p;
+        void* pl = (l < L - 1) ? ws.act[slot(l, 2)].p : nullptr;
+        if (p == LNR_FP32) {
+            conv_f32(u.convs[ci], (const float*)x, nullptr, (float*)t, nullptr, ws.B, W, H, st);
+            mark();
+            conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)s, (float*)pl, ws.B, W, H, st);
+            mark();
+        } else {
+            tc_conv(u.convs[ci], p, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            mark();
+            tc_conv(u.convs[ci + 1], p, t, nullptr, s, pl, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            mark();
+        }
+        ci += 2;
+        x = pl;
+    }
+    const void* deep = ws.act[slot(L - 1, 1)].p;
+    for (int l = L - 2; l >= 0; --l) {
+        const int W = ws.W >> l, H = ws.H >> l;
+        void* t = ws.act[slot(l, 0)].p;
+        void* d = ws.act[slot(l, 3)].p;
+        const void* skip = ws.act[slot(l, 1)].p;
+        if (p == LNR_FP32) {
+            conv_f32(u.convs[ci], (const float*)skip, (const float*)deep, (float*)t, nullptr, ws.B, W, H, st);
+            mark();
+            conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)d, nullptr, ws.B, W, H, st);
+            mark();
+        } else {
+            tc_conv(u.convs[ci], p, skip, deep, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            mark();
+            const bool last = (l == 0);
+            tc_conv(u.convs[ci + 1], p, t, nullptr, d, nullptr, last ? u.head_w : nullptr,
+                    last ? u.head_b : nullptr, last ? out : nullptr, ws.B, W, H, st);
+            mark();
+        }
+        ci += 2;
+        deep = d;
+    }
+    if (L == 1) deep = ws.act[slot(0, 1)].p;
+    if (p == LNR_FP32 || L == 1) {
+        size_t npx = (size_t)ws.B * ws.W * ws.H;
+        if (p == LNR_FP32)
+            k_head_f32<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>((const float*)deep, u.ch[0], u.head_w, u.head_b,
+                                                                      u.out_ch, out, npx);
+        mark();
+    }
+}
+
+// Convert the host weights (already batch-norm folded) to the device layouts.
+lnr_status unet_prepare(lnr_ctx* c) {
+    Unet& u = c->unet;
+    for (auto& L : u.convs) {
+        const int cin = L.cin0 + L.cin1;
+        const int cin_pad = (L.cin0 == 5 ? 8 : L.cin0) + L.cin1;
+        L.cin_pad = cin_pad;
+        std::vector<float> w((size_t)9 * cin_pad * L.cout, 0.f);
+        for (int co = 0; co < L.cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int t = 0; t < 9; ++t) w[((size_t)t * cin_pad + ci) * L.cout + co] = L.wf[((size_t)co * cin + ci) * 9 + t];
+        if (L.w32) cudaFree(L.w32);
+        if (L.b32) cudaFree(L.b32);
+        if (cudaMalloc(&L.w32, w.size() * 4) || cudaMalloc(&L.b32, L.cout * 4))
+            return fail(c, LNR_E_OOM, "U-Net weight upload");
+        cudaMemcpy(L.w32, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(L.b32, L.bf.data(), L.cout * 4, cudaMemcpyHostToDevice);
+        if (tc_available()) {
+            for (lnr_precision p : {LNR_BF16}) {
+                cudaError_t e = tc_prepare_layer(L, p);
+                if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core weight upload");
+            }
+        }
+    }
+    if (u.head_w) cudaFree(u.head_w);
+    if (u.head_b) cudaFree(u.head_b);
+    if (cudaMalloc(&u.head_w, u.head_wh.size() * 4) || cudaMalloc(&u.head_b, u.head_bh.size() * 4))
+        return fail(c, LNR_E_OOM, "U-Net head upload");
+    cudaMemcpy(u.head_w, u.head_wh.data(), u.head_wh.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(u.head_b, u.head_bh.data(), u.head_bh.size() * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "U-Net upload");
+    return LNR_OK;
+}
+
+}  // namespace lnr
