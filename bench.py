@@ -1,0 +1,340 @@
+"""Benchmark of the per-frame render path on the 20M-point multi-room scan at 1920x1080.
+
+Workload (multiroom_20M): 20,000,000 seeded synthetic points (12x12x4 m, 3x3 rooms, 8
+scanners, 1/r^2 density, per-scan colour offsets, georeferenced), grid cell 0.25 m,
+n_levels 5, filter_strength alternating 0.5 / 1.0, 4-level U-Net 32/64/128/256 with
+seeded He-init weights.  One step renders one batch of views through every stage of the
+path (cull, splat, resolve + pyramid, filter, U-Net); the cloud, grid and weights are
+resident in HBM before the timed region.  The grid build (once per cloud) is timed apart.
+
+Paths:
+  batched  : `--batch` views per launch, tensor-core U-Net (BF16) when the build has it,
+             else FP32 -- the headline `value`;
+  plain    : one view per call, FP32 U-Net -- reported beside it (`plain_fp32`).
+
+`--impl reference` times the CPU oracle (the method as plainly written; no GPU) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s & p99 latency, 20M pts: BF16 served vs FP32 plain, 1 GB300"
+W, H, NLEV, CELL = 1920, 1080, 5, 0.25
+CH = (32, 64, 128, 256)
+N_POINTS = 20_000_000
+FS = (0.5, 1.0)
+N_POSES = 16
+
+
+def unet_flops_per_px(ch, in_ch=5, out_ch=3):
+    """Algorithmic FLOPs of the U-Net per output pixel (2 per multiply-add)."""
+    L = len(ch)
+    mac = 0.0
+    cin = in_ch
+    for l in range(L):
+        mac += (9 * cin * ch[l] + 9 * ch[l] * ch[l]) / 4 ** l
+        cin = ch[l]
+    for l in range(L - 2, -1, -1):
+        mac += (9 * (ch[l] + ch[l + 1]) * ch[l] + 9 * ch[l] * ch[l]) / 4 ** l
+    mac += ch[0] * out_ch
+    return 2.0 * mac
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.dev = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def make_workload(device):
+    import synth
+    from synth.workloads import MULTIROOM_20M, make_scene
+    scene = make_scene(MULTIROOM_20M, device=device)
+    views = synth.random_poses(scene, N_POSES, seed=2)
+    weights = synth.unet_weights(CH, seed=1)
+    return scene, views, weights
+
+
+def cpu_sample(scene, views, weights, crop=(480, 272)):
+    """Oracle time of one 1080p frame: cull + splat + filter of a full view (one thread),
+    the FP64 U-Net on a crop scaled by pixel count to the full frame (all cores)."""
+    import oracle
+    import synth
+    g = oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
+    intr = synth.intrinsics_for(W, H)
+    t0 = time.perf_counter()
+    ref = oracle.render(g, views[0], intr, W, H, NLEV, FS[0])
+    t_raster = time.perf_counter() - t0
+    cw, chh = crop
+    x = ref["x"][(H - chh) // 2:(H - chh) // 2 + chh, (W - cw) // 2:(W - cw) // 2 + cw]
+    t0 = time.perf_counter()
+    oracle.unet(np.ascontiguousarray(x), CH, weights)
+    t_unet = (time.perf_counter() - t0) * (W * H) / (cw * chh)
+    s_per_frame = t_raster + t_unet
+    return {"value": 1.0 / s_per_frame, "unit": "frames/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"one 1920x1080 view: cull+splat+filter of the 20M-point scan on 1 core "
+                       f"({t_raster:.2f} s) + FP64 U-Net on a {cw}x{chh} crop scaled by pixel count "
+                       f"({t_unet:.1f} s per frame)")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, views, weights = make_workload("cpu")
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_sample(scene, [views[i % len(views)]], weights)
+        if i >= args.warmup:
+            times.append(1.0 / r["value"])
+    v = len(times) / sum(times)
+    cb = dict(r)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "multiroom_20M", "W": W, "H": H, "n_points": N_POINTS,
+                                             "n_levels": NLEV, "cell": CELL, "unet": list(CH)},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_2502_11618_gb300 as lnr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scene, views, weights = make_workload(dev)
+    stream = torch.cuda.Stream(device=dev)
+    r = lnr.Renderer(local, stream=stream.cuda_stream)
+    r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r.build_grid(CELL)
+    grid_ms = 1e3 * (time.perf_counter() - t0)
+    intr = synth.intrinsics_for(W, H)
+    have_tc = True
+    try:
+        r.set_unet(CH, weights, "bf16")
+    except lnr.LnrError:
+        have_tc = False
+        r.set_unet(CH, weights, "fp32")
+    prec = "bf16" if have_tc else "fp32"
+    B = args.batch
+    # every rank renders its own poses (replicas: views are independent)
+    pose = lambda i: views[(i * 7 + rank * 3) % len(views)]
+    out = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
+
+    def step(i):
+        vs = [pose(i * B + k) for k in range(B)]
+        fs = [FS[(i * B + k) % 2] for k in range(B)]
+        r.render_batch(vs, intr, W, H, NLEV, fs, out=out)
+
+    def timed(fn, K, Wm):
+        for i in range(Wm):
+            fn(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        t0 = time.perf_counter()
+        for i in range(K):
+            with torch.cuda.stream(stream):
+                evs[i][0].record(stream)
+            fn(Wm + i)
+            with torch.cuda.stream(stream):
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, wall
+
+    # ---- headline: batched path, device-timed --------------------------------------
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms, wall = timed(step, args.steps, args.warmup)
+    clk = clocks.stop()
+    tot_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    frames = B * args.steps * world
+    value = frames / (tot_ms / 1e3)
+
+    # ---- stage timing of the batched path (dominant kernel) ------------------------
+    r.set_timing(True)
+    tims = []
+    for i in range(3):
+        step(i)
+        torch.cuda.synchronize()
+        tims.append(r.get_timing())
+    r.set_timing(False)
+    unet_ms = float(np.median([t["unet"] for t in tims]))
+    splat_ms = float(np.median([t["splat"] for t in tims]))
+    pk = peaks()
+    flops = unet_flops_per_px(CH) * W * H * B
+    if have_tc:
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof = {"kernel": "conv3x3 tcgen05 (all U-Net conv launches)", "bound": "tensor",
+                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+    else:
+        smax = (clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * smax * 1e6 / 1e12
+        roof = {"kernel": "conv3x3 FP32 SIMT (all U-Net conv launches)", "bound": "alu",
+                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+
+    # ---- plain per-frame FP32 path -------------------------------------------------
+    r.set_precision("fp32")
+    out1 = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+
+    def step_plain(i):
+        r.render(pose(i), intr, W, H, NLEV, FS[i % 2], out=out1)
+
+    plain_ms, _ = timed(step_plain, max(3, args.steps // 2), 3)
+    plain_fps = 1e3 / float(np.mean(plain_ms))
+
+    # ---- end to end through the public API, host buffers ---------------------------
+    r.set_precision(prec)
+    host_out = np.empty((B, H, W, 3), np.float32)
+    for i in range(2):
+        r.render_batch([pose(k) for k in range(B)], intr, W, H, NLEV, [FS[k % 2] for k in range(B)], out=host_out)
+    Ke = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for i in range(Ke):
+        r.render_batch([pose(i * B + k) for k in range(B)], intr, W, H, NLEV,
+                       [FS[(i * B + k) % 2] for k in range(B)], out=host_out)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": B * Ke / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": B * (96 + 24 + 4), "d2h_bytes_per_step": int(host_out.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(scene, views, weights)
+
+    launches_per_step = 3 + 1 + 1 + NLEV + 2 * (2 * len(CH) - 1) + (0 if have_tc else 1)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if have_tc else "f32", "data": "synthetic",
+            "config": {"workload": "multiroom_20M", "W": W, "H": H, "n_points": N_POINTS, "views_per_step": B,
+                       "n_levels": NLEV, "filter_strength": list(FS), "cell": CELL, "unet": list(CH),
+                       "precision": prec, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2: per-step working set > 1 GB, every step new poses"},
+            "latency_ms": {"batched": {"p50": float(np.percentile(step_ms, 50)),
+                                       "p99": float(np.percentile(step_ms, 99))},
+                           "plain_fp32": {"p50": float(np.percentile(plain_ms, 50)),
+                                          "p99": float(np.percentile(plain_ms, 99))}},
+            "plain_fp32": {"value": plain_fps, "unit": "frames/s"},
+            "stages_ms_per_batch": {k: round(float(np.median([t[k] for t in tims])), 4)
+                                    for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]},
+            "grid_build_ms": grid_ms,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

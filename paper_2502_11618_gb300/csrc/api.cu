@@ -193,6 +193,8 @@ static lnr_status finish_output(lnr_ctx* c, Workspace& ws, float* out, size_t nf
         if (e != cudaSuccess) return cuda_fail(c, e, "render");
     }
     if (c->timing) read_timing(c, ws);
+    if ((!on_device || c->timing) && c->prec != LNR_FP32 && tc_error_word())
+        return fail(c, LNR_E_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait ran out)");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
     return LNR_OK;
@@ -398,9 +400,9 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
     c->unet_ok = true;
     c->prec = prec;
     c->unet_gen++;
-    if (prec != LNR_FP32 && !tc_available()) {
+    if ((prec != LNR_FP32 && !tc_available()) || prec == LNR_FP8 || (prec != LNR_FP32 && L < 2)) {
         c->prec = LNR_FP32;
-        return fail(c, LNR_E_ARG, "tensor-core precision not available in this build");
+        return fail(c, LNR_E_ARG, "precision not available for this net in this build");
     }
     return LNR_OK;
 }
@@ -409,7 +411,8 @@ lnr_status lnr_set_precision(lnr_ctx* c, lnr_precision prec) {
     if (!c) return LNR_E_ARG;
     if (!c->unet_ok) return fail(c, LNR_E_STATE, "set_precision before set_unet");
     if (prec < LNR_FP32 || prec > LNR_FP8) return fail(c, LNR_E_ARG, "bad precision");
-    if (prec != LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "tensor-core precision not available");
+    if ((prec != LNR_FP32 && !tc_available()) || prec == LNR_FP8 || (prec != LNR_FP32 && c->unet.levels < 2))
+        return fail(c, LNR_E_ARG, "precision not available for this net in this build");
     c->prec = prec;
     return LNR_OK;
 }

@@ -1,13 +1,533 @@
-// Tensor-core (tcgen05) convolutions: placeholder until the BF16 / FP8 kernels land.
+// U-Net 3x3 convolutions on the 5th-generation tensor cores (tcgen05 + TMEM), fed by TMA
+// (Fig. 1; Sec. 3, "U-Net Reconstruction").
+//
+// Each convolution is an implicit GEMM: D[128 output pixels][Cout] += A[pixels][K] B[Cout][K]^T
+// with K = 9 taps x input channels.  A tile of A is one TMA box of the NHWC activation
+// tensor shifted by the tap; out-of-image rows and columns are zero-filled by TMA, which
+// gives the convolution's zero padding for free.  Weights are K-major [Cout][tap][Cin].
+//
+// Fusions:
+//  - encoder convs below the bottleneck also write the 2x2 max-pooled output (the tile is
+//    2 rows x 64 pixels, so every pooling quad lies in one tile);
+//  - the first decoder conv of each level reads the skip tensor and the nearest-2x-
+//    upsampled deeper tensor directly, never materialising the concatenation: its output
+//    tile is 128 pixels of one parity class (x mod 2, y mod 2), for which the upsampled
+//    operand of every tap is a plain row of the coarse tensor and the skip operand a
+//    stride-2 row of the fine one (a 5-D TMA view);
+//  - the last decoder conv applies the 1x1 head and the sigmoid in its epilogue.
+//
+// Kernel structure (persistent, one CTA per SM, 6 warps):
+//  warp 0   TMA producer: A and B tiles into an S-stage shared-memory ring;
+//  warp 1   MMA issuer: tcgen05.mma kind::f16 (BF16 in, FP32 accumulate) into one of two
+//           TMEM accumulators, tcgen05.commit to free ring stages and publish results;
+//  warps 2-5 epilogue: tcgen05.ld, bias, ReLU, BF16 store (+ pool / head).
+// Every mbarrier wait is bounded (about 2 s); a wait that runs out sets an error word and
+// the CTA drains its copies, frees its TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
 #include "lnr_internal.h"
 
 namespace lnr {
+namespace {
 
-bool tc_available() { return false; }
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
 
-cudaError_t tc_prepare_layer(ConvLayer&, lnr_precision) { return cudaErrorNotSupported; }
+struct Seg {
+    CUtensorMap a;   // activation view of this K segment's source
+    CUtensorMap b;   // weight view with box {kc, N}
+    int kind;        // 0: same-resolution source (2x64 tiles); 1: skip, parity tiles; 2: coarse, parity tiles
+    int kc;          // channels per K chunk: 16, 32 or 64
+    int nchunk;      // chunks per tap
+    int koff;        // K offset of the segment inside one tap
+    uint32_t bytes;  // A + B bytes of one chunk
+    uint32_t swz;    // UMMA layout type of the chunk (SW32 = 6, SW64 = 4, SW128 = 2)
+    uint32_t sbo;    // bytes between 8-row core-matrix groups
+};
 
-void tc_conv(const ConvLayer&, lnr_precision, const void*, const void*, void*, void*, const float*,
-             const float*, float*, int, int, int, cudaStream_t) {}
+struct Params {
+    Seg seg[2];
+    int nseg;
+    int parity;       // 1: decoder parity tiles, 0: 2 x 64 pixel tiles
+    int W, H, B, N, cin_pad;
+    int tiles_x, tiles_y, ntiles;
+    int stages;
+    uint32_t stage_bytes, a_region, xch_bytes, tmem_cols, idesc;
+    const float* bias;
+    __nv_bfloat16* out;
+    __nv_bfloat16* pool_out;
+    const float* head_w;
+    const float* head_b;
+    float* head_out;
+    int head_o;
+    int* err;
+};
+
+// ------------------------------------------------------------- PTX wrappers ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity`: false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2, int c3,
+                                       int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// UMMA shared-memory descriptor of a K-major, swizzled operand tile.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo, uint32_t swz) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)swz << 61);
+}
+
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+struct TileCoord {
+    int n, x0, y0;    // standard tiles: image, first column, first row
+    int cx0, cy, px, py;  // parity tiles: first coarse column, coarse row, parity
+};
+
+__device__ __forceinline__ TileCoord decode(const Params& p, int t) {
+    TileCoord c{};
+    const int tx = t % p.tiles_x;
+    int r = t / p.tiles_x;
+    const int ty = r % p.tiles_y;
+    r /= p.tiles_y;
+    if (p.parity) {
+        const int par = r & 3;
+        c.n = r >> 2;
+        c.px = par & 1;
+        c.py = par >> 1;
+        c.cx0 = tx * 128;
+        c.cy = ty;
+    } else {
+        c.n = r;
+        c.x0 = tx * 64;
+        c.y0 = ty * 2;
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ Params p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* const gbase = smem_raw + (base - raw);
+    const int S = p.stages;
+    float* xch = reinterpret_cast<float*>(gbase + S * p.stage_bytes);
+    const uint32_t bars = base + S * p.stage_bytes + p.xch_bytes;
+    auto full = [&](int s) { return bars + 8u * s; };
+    auto empty = [&](int s) { return bars + 8u * (S + s); };
+    auto tfull = [&](int b) { return bars + 8u * (2 * S + b); };
+    auto tempty = [&](int b) { return bars + 8u * (2 * S + 2 + b); };
+    const uint32_t drain = bars + 8u * (2 * S + 4);
+    const uint32_t tslot = bars + 8u * (2 * S + 5);
+    volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), 4);
+        }
+        mbar_init(drain, 1);
+        *flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ producer --
+        int use = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            const TileCoord c = decode(p, t);
+            for (int tap = 0; tap < 9 && ok; ++tap) {
+                const int ky = tap / 3, kx = tap % 3;
+                for (int sg = 0; sg < p.nseg && ok; ++sg) {
+                    const Seg& s = p.seg[sg];
+                    for (int cc = 0; cc < s.nchunk; ++cc) {
+                        const int st = use % S;
+                        if (!mbar_wait(empty(st), ((use / S) & 1) ^ 1)) { ok = false; break; }
+                        const uint32_t a_dst = base + st * p.stage_bytes, b_dst = a_dst + p.a_region;
+                        mbar_expect_tx(full(st), s.bytes);
+                        const int cb = cc * s.kc;
+                        if (s.kind == 0) {
+                            tma_4d(a_dst, &s.a, full(st), cb, c.x0 + kx - 1, c.y0 + ky - 1, c.n);
+                        } else if (s.kind == 1) {
+                            const int dxf = c.px + kx - 1;
+                            tma_5d(a_dst, &s.a, full(st), cb, dxf & 1, c.cx0 + (dxf >> 1), 2 * c.cy + c.py + ky - 1, c.n);
+                        } else {
+                            tma_4d(a_dst, &s.a, full(st), cb, c.cx0 + ((c.px + kx - 1) >> 1), c.cy + ((c.py + ky - 1) >> 1),
+                                   c.n);
+                        }
+                        tma_2d(b_dst, &s.b, full(st), tap * p.cin_pad + s.koff + cb, 0);
+                        ++use;
+                    }
+                }
+            }
+        }
+        if (!ok) atomicExch(p.err, 1);
+        // no copy may still be in flight when the CTA exits
+        for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // ----------------------------------------------------------------- MMA --
+        int use = 0, tcount = 0;
+        bool ok = true, issued = false;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
+            const int b = tcount & 1;
+            if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(b * p.N);
+            uint32_t acc = 0;
+            for (int tap = 0; tap < 9 && ok; ++tap)
+                for (int sg = 0; sg < p.nseg && ok; ++sg) {
+                    const Seg& s = p.seg[sg];
+                    for (int cc = 0; cc < s.nchunk; ++cc) {
+                        const int st = use % S;
+                        if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a_addr = base + st * p.stage_bytes, b_addr = a_addr + p.a_region;
+                        for (int k = 0; k < s.kc / 16; ++k) {
+                            mma_bf16(d, sdesc(a_addr + 32u * k, s.sbo, s.swz), sdesc(b_addr + 32u * k, s.sbo, s.swz),
+                                     p.idesc, acc);
+                            acc = 1;
+                        }
+                        issued = true;
+                        mma_commit(empty(st));
+                        ++use;
+                    }
+                }
+            if (ok) mma_commit(tfull(b));
+        }
+        if (!ok) atomicExch(p.err, 2);
+        if (issued) {  // every MMA issued has completed before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------ epilogue --
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int m = 32 * q + lane;     // tile row of this thread
+        const bool leader = threadIdx.x == 64;
+        const int Wh = p.W >> 1, Hh = p.H >> 1;
+        int tcount = 0;
+        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
+            const int b = tcount & 1;
+            if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
+            named_sync(1, 128);
+            if (*flag) break;
+            tc_fence_after();
+            const TileCoord c = decode(p, t);
+            int x, y;
+            if (p.parity) {
+                x = 2 * (c.cx0 + m) + c.px;
+                y = 2 * c.cy + c.py;
+            } else {
+                x = c.x0 + (m & 63);
+                y = c.y0 + (m >> 6);
+            }
+            const bool valid = x < p.W && y < p.H;
+            const size_t pix = ((size_t)c.n * p.H + y) * p.W + x;
+            float h[4] = {0.f, 0.f, 0.f, 0.f};
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * p.N);
+            for (int c0 = 0; c0 < p.N; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + __ldg(p.bias + c0 + j), 0.f);
+                if (p.head_out) {
+                    for (int o = 0; o < p.head_o; ++o) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) s = fmaf(__ldg(p.head_w + o * p.N + c0 + j), v[j], s);
+                        h[o] += s;
+                    }
+                } else if (valid) {
+                    uint4 pk[2];
+                    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        pw[j] = *reinterpret_cast<uint32_t*>(&b2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(p.out + pix * p.N + c0);
+                    dst[0] = pk[0];
+                    dst[1] = pk[1];
+                }
+                if (p.pool_out) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) xch[m * kXchStride + j] = v[j];
+                    named_sync(1, 128);
+                    if (m < 64 && (m & 1) == 0 && valid) {
+                        uint4 pk[2];
+                        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float a0 = fmaxf(fmaxf(xch[m * kXchStride + 2 * j], xch[(m + 1) * kXchStride + 2 * j]),
+                                             fmaxf(xch[(m + 64) * kXchStride + 2 * j], xch[(m + 65) * kXchStride + 2 * j]));
+                            float a1 = fmaxf(fmaxf(xch[m * kXchStride + 2 * j + 1], xch[(m + 1) * kXchStride + 2 * j + 1]),
+                                             fmaxf(xch[(m + 64) * kXchStride + 2 * j + 1],
+                                                   xch[(m + 65) * kXchStride + 2 * j + 1]));
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
+                            pw[j] = *reinterpret_cast<uint32_t*>(&b2);
+                        }
+                        const size_t pp = ((size_t)c.n * Hh + (y >> 1)) * Wh + (x >> 1);
+                        uint4* dst = reinterpret_cast<uint4*>(p.pool_out + pp * p.N + c0);
+                        dst[0] = pk[0];
+                        dst[1] = pk[1];
+                    }
+                    named_sync(1, 128);
+                }
+            }
+            if (p.head_out && valid) {
+                for (int o = 0; o < p.head_o; ++o) {
+                    const float z = h[o] + __ldg(p.head_b + o);
+                    p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-z));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(b));
+        }
+        if (leader && *flag) atomicExch(p.err, 3);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------ host side ----
+
+CUtensorMapSwizzle swizzle_for(int kc) {
+    return kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+uint32_t umma_layout_for(int kc) { return kc == 64 ? 2u : kc == 32 ? 4u : 6u; }
+
+bool encode(CUtensorMap* m, int rank, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
+            const cuuint32_t* box, int kc) {
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims,
+                                        strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(kc),
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int g_num_sms = 0;
+int* g_err = nullptr;
+int g_host_err = 0;  // a tensor map could not be encoded: the launch was skipped
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+// Channels a layer's first source carries in the tensor-core layout (the RGBDA input is
+// padded to 16 so that every K chunk is one 32-byte MMA step).
+static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 16 : L.cin0; }
+
+cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p) {
+    if (p != LNR_BF16) return cudaErrorNotSupported;
+    const int c0 = tc_c0(L), cin = L.cin0 + L.cin1, cpad = c0 + L.cin1;
+    std::vector<__nv_bfloat16> w((size_t)L.cout * 9 * cpad, __float2bfloat16(0.f));
+    for (int co = 0; co < L.cout; ++co)
+        for (int ci = 0; ci < cin; ++ci) {
+            const int k = ci < L.cin0 ? ci : c0 + (ci - L.cin0);
+            for (int t = 0; t < 9; ++t)
+                w[((size_t)co * 9 + t) * cpad + k] = __float2bfloat16(L.wf[((size_t)co * cin + ci) * 9 + t]);
+        }
+    if (L.wtc) cudaFree(L.wtc);
+    L.wtc = nullptr;
+    cudaError_t e = cudaMalloc(&L.wtc, w.size() * 2);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(L.wtc, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
+}
+
+void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
+             const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
+             cudaStream_t st) {
+    (void)prec;
+    if (!g_num_sms) {
+        int dev;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaMalloc(&g_err, sizeof(int));
+        cudaMemset(g_err, 0, sizeof(int));
+        cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    }
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    const int N = L.cout;
+    const int c0 = tc_c0(L), cpad = c0 + L.cin1;
+    p.N = N;
+    p.W = W;
+    p.H = H;
+    p.B = B;
+    p.cin_pad = cpad;
+    p.parity = L.cin1 > 0;
+    const cuuint64_t Ktot = 9ull * cpad;
+    auto set_seg = [&](Seg& s, int kind, const void* src, int C, int koff, int Ws, int Hs) {
+        s.kind = kind;
+        s.kc = C >= 64 ? 64 : C;
+        s.nchunk = C / s.kc;
+        s.koff = koff;
+        s.swz = umma_layout_for(s.kc);
+        s.sbo = 16u * s.kc;  // 8 rows x (kc x 2 bytes)
+        s.bytes = (uint32_t)(128 + N) * s.kc * 2;
+        const cuuint64_t eb = 2;
+        if (kind == 1) {
+            cuuint64_t dims[5] = {(cuuint64_t)C, 2, (cuuint64_t)Ws / 2, (cuuint64_t)Hs, (cuuint64_t)B};
+            cuuint64_t str[4] = {C * eb, 2 * C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
+            cuuint32_t box[5] = {(cuuint32_t)s.kc, 1, 128, 1, 1};
+            if (!encode(&s.a, 5, src, dims, str, box, s.kc)) g_host_err = 4;
+        } else {
+            cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
+            cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
+            cuuint32_t box[4] = {(cuuint32_t)s.kc, kind == 0 ? 64u : 128u, kind == 0 ? 2u : 1u, 1};
+            if (!encode(&s.a, 4, src, dims, str, box, s.kc)) g_host_err = 4;
+        }
+        cuuint64_t wd[2] = {Ktot, (cuuint64_t)N};
+        cuuint64_t ws_[1] = {Ktot * eb};
+        cuuint32_t wb[2] = {(cuuint32_t)s.kc, (cuuint32_t)N};
+        if (!encode(&s.b, 2, L.wtc, wd, ws_, wb, s.kc)) g_host_err = 4;
+    };
+    if (p.parity) {
+        p.nseg = 2;
+        set_seg(p.seg[0], 1, src0, c0, 0, W, H);
+        set_seg(p.seg[1], 2, src1, L.cin1, c0, W / 2, H / 2);
+        p.tiles_x = (W / 2 + 127) / 128;
+        p.tiles_y = H / 2;
+        p.ntiles = B * 4 * p.tiles_y * p.tiles_x;
+    } else {
+        p.nseg = 1;
+        set_seg(p.seg[0], 0, src0, c0, 0, W, H);
+        p.tiles_x = (W + 63) / 64;
+        p.tiles_y = (H + 1) / 2;
+        p.ntiles = B * p.tiles_y * p.tiles_x;
+    }
+    int kc_max = 0;
+    for (int i = 0; i < p.nseg; ++i) kc_max = std::max(kc_max, p.seg[i].kc);
+    p.a_region = (uint32_t)(128 * kc_max * 2);
+    const uint32_t b_region = (uint32_t)((N * kc_max * 2 + 1023) & ~1023);
+    p.stage_bytes = p.a_region + b_region;
+    p.xch_bytes = pool_out ? (uint32_t)((128 * kXchStride * 4 + 1023) & ~1023) : 0;
+    const uint32_t budget = 220 * 1024 - p.xch_bytes;
+    p.stages = std::min<int>(8, budget / p.stage_bytes);
+    uint32_t cols = 32;
+    while (cols < 2u * N) cols <<= 1;
+    p.tmem_cols = cols;
+    p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    p.bias = L.b32;
+    p.out = static_cast<__nv_bfloat16*>(out);
+    p.pool_out = static_cast<__nv_bfloat16*>(pool_out);
+    p.head_w = head_w;
+    p.head_b = head_b;
+    p.head_out = head_out;
+    p.head_o = head_o;
+    p.err = g_err;
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + p.xch_bytes + 8 * (2 * p.stages + 6) + 16;
+    const int grid = std::min(p.ntiles, g_num_sms);
+    if (g_host_err || !L.wtc) return;
+    k_conv_tc<<<grid, kThreads, smem, st>>>(p);
+}
+
+int tc_error_word() {
+    if (g_host_err) {
+        const int h = g_host_err;
+        g_host_err = 0;
+        return h;
+    }
+    if (!g_err) return 0;
+    int h = 0;
+    cudaMemcpy(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (h) cudaMemset(g_err, 0, sizeof(int));
+    return h;
+}
 
 }  // namespace lnr

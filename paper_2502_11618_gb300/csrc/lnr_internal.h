@@ -171,7 +171,7 @@ void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_clear_keys(Workspace& ws, cudaStream_t st);
 void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
-// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC8, 2 = none (stage taps only).
+// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC16, 2 = none (stage taps only).
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,
                      bool write_u0, cudaStream_t st);
 size_t pyramid_floats(int W, int H, int nlev);
@@ -190,6 +190,7 @@ bool tc_available();
 cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p);
 void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out,
              void* pool_out, const float* head_w, const float* head_b, float* head_out, int B,
-             int W, int H, cudaStream_t st);
+             int W, int H, int head_o, cudaStream_t st);
+int tc_error_word();  // nonzero after a bounded wait in a tensor-core kernel ran out (then reset)
 
 }  // namespace lnr

@@ -365,7 +365,7 @@ struct UpArgs {
     int fill;            // non-final level: fill empty pixels by interpolation
     // final level only
     const uint32_t* rgba;
-    void* unet_in;       // NHWC, 8 channels
+    void* unet_in;       // NHWC: 8 FP32 channels (kind 0) or 16 BF16 channels (kind 1)
     int kind;            // 0 = FP32, 1 = BF16, 2 = none
     float* u0;           // kept depth tap (nullable)
 };
@@ -384,7 +384,8 @@ __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, fl
         u.y = *reinterpret_cast<uint32_t*>(&v1);
         u.z = *reinterpret_cast<uint32_t*>(&v2);
         u.w = *reinterpret_cast<uint32_t*>(&v3);
-        reinterpret_cast<uint4*>(base)[q] = u;
+        reinterpret_cast<uint4*>(base)[2 * q] = u;
+        reinterpret_cast<uint4*>(base)[2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -493,7 +494,7 @@ __global__ void k_extract5(const void* in, int kind, float* out, int64_t npx) {
     for (int c = 0; c < 5; ++c) {
         float v;
         if (kind == 0) v = static_cast<const float*>(in)[q * 8 + c];
-        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 8 + c]);
+        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 16 + c]);
         out[q * 5 + c] = v;
     }
 }

@@ -149,9 +149,12 @@ void conv_f32(const ConvLayer& L, const float* src0, const float* src1, float* o
     if (L.cout % 64 == 0) {
         dim3 g((W + 63) / 64, (H + 1) / 2, B * (L.cout / 64));
         k_conv3x3_f32<64, 64><<<g, 256, 0, st>>>(a);
-    } else {
+    } else if (L.cout % 32 == 0) {
         dim3 g((W + 127) / 128, (H + 1) / 2, B * (L.cout / 32));
         k_conv3x3_f32<128, 32><<<g, 256, 0, st>>>(a);
+    } else {
+        dim3 g((W + 255) / 256, (H + 1) / 2, B * (L.cout / 16));
+        k_conv3x3_f32<256, 16><<<g, 256, 0, st>>>(a);
     }
 }
 
@@ -211,9 +214,9 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
             conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)s, (float*)pl, ws.B, W, H, st);
             mark();
         } else {
-            tc_conv(u.convs[ci], p, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            tc_conv(u.convs[ci], p, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
             mark();
-            tc_conv(u.convs[ci + 1], p, t, nullptr, s, pl, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            tc_conv(u.convs[ci + 1], p, t, nullptr, s, pl, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
             mark();
         }
         ci += 2;
@@ -231,11 +234,11 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
             conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)d, nullptr, ws.B, W, H, st);
             mark();
         } else {
-            tc_conv(u.convs[ci], p, skip, deep, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, st);
+            tc_conv(u.convs[ci], p, skip, deep, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
             mark();
             const bool last = (l == 0);
             tc_conv(u.convs[ci + 1], p, t, nullptr, d, nullptr, last ? u.head_w : nullptr,
-                    last ? u.head_b : nullptr, last ? out : nullptr, ws.B, W, H, st);
+                    last ? u.head_b : nullptr, last ? out : nullptr, ws.B, W, H, u.out_ch, st);
             mark();
         }
         ci += 2;

@@ -1,0 +1,93 @@
+"""BF16 tensor-core U-Net (tcgen05 + TMA) against the CPU oracle's FP64 U-Net.
+
+Bars: max abs error <= 2e-2 and PSNR >= 45 dB per view, outputs in [0, 1].  The
+upstream stages are shared with the FP32 path and stay bit-exact (checked there).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+BF16_MAXABS = 2e-2
+BF16_PSNR = 45.0
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+@pytest.fixture(scope="module")
+def lnr():
+    import paper_2502_11618_gb300 as p
+    from paper_2502_11618_gb300 import build
+    build.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def room():
+    s = synth.room_scene()
+    return s, oracle.build_grid(s.xyz, s.rgb, s.scan_id, 0.5)
+
+
+def _renderer(lnr, s, cell, ch, w, prec):
+    r = lnr.Renderer(0)
+    r.load_cloud(s.xyz, s.rgb, s.scan_id)
+    r.build_grid(cell)
+    r.set_unet(ch, w, prec)
+    return r
+
+
+def test_bf16_room_three_levels(lnr, room):
+    s, g = room
+    ch = (16, 32, 64)
+    w = synth.unet_weights(ch, seed=1)
+    r = _renderer(lnr, s, 0.5, ch, w, "bf16")
+    W, H = 256, 256
+    intr = synth.intrinsics_for(W, H)
+    for view in synth.random_poses(s, 3, seed=2):
+        ref = oracle.render(g, view, intr, W, H, 3, 1.0, w, ch)
+        y = r.render(view, intr, W, H, 3, 1.0)
+        err = np.abs(y - ref["y"]).max()
+        assert 0.0 <= y.min() and y.max() <= 1.0
+        assert err <= BF16_MAXABS, err
+        assert psnr(y, ref["y"]) >= BF16_PSNR
+    r.close()
+
+
+def test_bf16_multiroom_four_levels_ragged(lnr):
+    s = synth.multiroom_scene(n_points=1_000_000)
+    g = oracle.build_grid(s.xyz, s.rgb, s.scan_id, 0.25)
+    ch = (32, 64, 128, 256)
+    w = synth.unet_weights(ch, seed=1)
+    r = _renderer(lnr, s, 0.25, ch, w, "bf16")
+    W, H = 328, 200            # several tiles and a ragged tail at every level
+    intr = synth.intrinsics_for(W, H)
+    for view in synth.random_poses(s, 2, seed=2):
+        ref = oracle.render(g, view, intr, W, H, 4, 0.5, w, ch)
+        y = r.render(view, intr, W, H, 4, 0.5)
+        assert np.abs(y - ref["y"]).max() <= BF16_MAXABS
+        assert psnr(y, ref["y"]) >= BF16_PSNR
+    r.close()
+
+
+def test_bf16_batch_equals_single_and_precision_switch(lnr, room):
+    s, g = room
+    ch = (16, 32, 64)
+    w = synth.unet_weights(ch, seed=1)
+    r = _renderer(lnr, s, 0.5, ch, w, "bf16")
+    W, H = 128, 96
+    intr = synth.intrinsics_for(W, H)
+    views = synth.random_poses(s, 3, seed=4)
+    yb = r.render_batch(views, intr, W, H, 3, [1.0, 0.5, 1.5])
+    for i, v in enumerate(views):
+        assert np.array_equal(yb[i], r.render(v, intr, W, H, 3, [1.0, 0.5, 1.5][i]))
+    r.set_precision("fp32")
+    y32 = r.render(views[0], intr, W, H, 3, 1.0)
+    ref = oracle.render(g, views[0], intr, W, H, 3, 1.0, w, ch)
+    assert np.abs(y32 - ref["y"]).max() <= 1e-4
+    r.close()
