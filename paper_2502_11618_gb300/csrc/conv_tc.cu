@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "lnr_internal.h"
@@ -384,6 +385,301 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     }
 }
 
+// ================================================================ halo kernel ==
+//
+// The same convolution with the input staged ONCE per tile: a tile is R output rows x 128
+// columns; for every K chunk of CK channels the producer loads the input halo (R+2 rows x
+// 130 columns, or the parity-class rows for the decoder's first conv) in the MMA's
+// no-swizzle K-major layout (8-channel blocks, 16 bytes per pixel, pixels at 16-byte
+// pitch), plus the chunk's weights for all 9 taps.  Every tap is then just a descriptor
+// offset into the staged halo (one pixel = 16 bytes, one row = 130 pixels), so the 9 taps
+// x R rows of MMAs read the halo that was fetched once.  The R accumulators of a tile sit
+// side by side in TMEM (R*N columns, double-buffered).
+// 2x2 pooling needs no shared-memory exchange: a thread owns one column of R rows, and
+// its horizontal neighbour is the adjacent lane.
+
+constexpr int kHaloW = 130;                 // staged pixels per halo row
+constexpr uint32_t kHaloRowBytes = kHaloW * 16;
+
+struct HSeg {
+    CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {8, 130, rows, 1}; kind 1: 5-D, box {8, 1, 130, rows, 1}
+    int kind;        // 0: same-resolution source; 1: skip (parity tiles); 2: coarse (parity tiles)
+    int rows;        // halo rows staged per 8-channel block
+    int nchunk;      // K chunks of this segment
+    int chunk0;      // global index of its first chunk (weights are stored chunk-major)
+    uint32_t blk;    // bytes of one staged 8-channel block (128-byte aligned)
+    uint32_t a_bytes;
+};
+
+struct HParams {
+    HSeg seg[2];
+    int nseg;
+    int CK, R, parity, W, H, B, N;
+    int tiles_x, tiles_y, ntiles;
+    const __nv_bfloat16* wB;   // [chunk][tap][CK/8][N][8]
+    uint32_t b_bytes;          // 9 * N * CK * 2
+    int stages;
+    uint32_t stage_bytes, a_region, tmem_cols, idesc;
+    const float* bias;
+    __nv_bfloat16* out;
+    __nv_bfloat16* pool_out;
+    const float* head_w;
+    const float* head_b;
+    float* head_out;
+    int head_o;
+    int* err;
+};
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// UMMA descriptor of a no-swizzle K-major tile: 8-row x 16-byte core matrices, LBO between
+// K-adjacent core matrices, SBO between 8-row groups.
+__device__ __forceinline__ uint64_t ndesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
+    uint4 pk[2];
+    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        pw[j] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+    reinterpret_cast<uint4*>(dst)[0] = pk[0];
+    reinterpret_cast<uint4*>(dst)[1] = pk[1];
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* const gbase = smem_raw + (base - raw);
+    const int S = p.stages;
+    const uint32_t bars = base + S * p.stage_bytes;
+    auto full = [&](int s) { return bars + 8u * s; };
+    auto empty = [&](int s) { return bars + 8u * (S + s); };
+    auto tfull = [&](int b) { return bars + 8u * (2 * S + b); };
+    auto tempty = [&](int b) { return bars + 8u * (2 * S + 2 + b); };
+    const uint32_t drain = bars + 8u * (2 * S + 4);
+    const uint32_t tslot = bars + 8u * (2 * S + 5);
+    volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = p.R, N = p.N, CK = p.CK;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), 4);
+        }
+        mbar_init(drain, 1);
+        *flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
+    const int nchunks = p.seg[0].nchunk + (p.nseg > 1 ? p.seg[1].nchunk : 0);
+
+    auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
+        const int tx = t % p.tiles_x;
+        int r = t / p.tiles_x;
+        const int ty = r % p.tiles_y;
+        r /= p.tiles_y;
+        if (p.parity) {
+            px = r & 1;
+            py = (r >> 1) & 1;
+            n = r >> 2;
+        } else {
+            px = py = 0;
+            n = r;
+        }
+        x0 = tx * 128;   // first (coarse, for parity tiles) column
+        y0 = ty * R;     // first (coarse, for parity tiles) row
+    };
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ producer --
+        int use = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            int n, x0, y0, px, py;
+            tile_of(t, n, x0, y0, px, py);
+            for (int sg = 0; sg < p.nseg && ok; ++sg) {
+                const HSeg& s = p.seg[sg];
+                for (int cc = 0; cc < s.nchunk; ++cc) {
+                    const int st = use % S;
+                    if (!mbar_wait(empty(st), ((use / S) & 1) ^ 1)) { ok = false; break; }
+                    const uint32_t a_dst = base + st * p.stage_bytes;
+                    mbar_expect_tx(full(st), s.a_bytes + p.b_bytes);
+                    for (int j = 0; j < CK / 8; ++j) {
+                        const int c8 = cc * CK + 8 * j;
+                        if (s.kind == 0) {
+                            tma_4d(a_dst + j * s.blk, &s.a, full(st), c8, x0 - 1, y0 - 1, n);
+                        } else if (s.kind == 2) {
+                            tma_4d(a_dst + j * s.blk, &s.a, full(st), c8, x0 - 1, y0 - 1, n);
+                        } else {
+                            for (int sx = 0; sx < 2; ++sx)
+                                tma_5d(a_dst + (2 * j + sx) * s.blk, &s.a, full(st), c8, sx, x0 - 1, 2 * y0 + py - 1, n);
+                        }
+                    }
+                    bulk_g2s(a_dst + p.a_region, p.wB + (size_t)(s.chunk0 + cc) * (p.b_bytes / 2), p.b_bytes, full(st));
+                    ++use;
+                }
+            }
+        }
+        if (!ok) atomicExch(p.err, 5);
+        for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // ----------------------------------------------------------------- MMA --
+        int use = 0, tcount = 0;
+        bool ok = true, issued = false;
+        const uint32_t bsbo = 128, blbo = (uint32_t)N * 16;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
+            int n, x0, y0, px, py;
+            tile_of(t, n, x0, y0, px, py);
+            const int b = tcount & 1;
+            if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d0 = tmem + (uint32_t)(b * R * N);
+            int kc_global = 0;
+            for (int sg = 0; sg < p.nseg && ok; ++sg) {
+                const HSeg& s = p.seg[sg];
+                for (int cc = 0; cc < s.nchunk; ++cc, ++kc_global) {
+                    const int st = use % S;
+                    if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_base = base + st * p.stage_bytes, b_base = a_base + p.a_region;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap % 3;
+                        // halo offset of this tap for output row 0, and the K-pair stride (LBO)
+                        uint32_t off, lbo, rstep;
+                        if (s.kind == 0) {
+                            off = ky * kHaloRowBytes + kx * 16;
+                            lbo = s.blk;
+                            rstep = kHaloRowBytes;
+                        } else if (s.kind == 2) {
+                            const int dx = (px + kx - 1) >> 1, dy = (py + ky - 1) >> 1;
+                            off = (1 + dy) * kHaloRowBytes + (1 + dx) * 16;
+                            lbo = s.blk;
+                            rstep = kHaloRowBytes;
+                        } else {
+                            const int dxf = px + kx - 1;
+                            off = (dxf & 1) * s.blk + ky * kHaloRowBytes + (1 + (dxf >> 1)) * 16;
+                            lbo = 2 * s.blk;
+                            rstep = 2 * kHaloRowBytes;
+                        }
+                        for (int k16 = 0; k16 < CK / 16; ++k16) {
+                            const uint64_t bd = ndesc(b_base + (uint32_t)((tap * (CK / 8) + 2 * k16) * N * 16), blbo, bsbo);
+                            const uint32_t ak = a_base + 2 * k16 * lbo + off;
+                            const uint32_t acc = (kc_global | tap | k16) ? 1u : 0u;
+                            for (int r = 0; r < R; ++r)
+                                mma_bf16(d0 + (uint32_t)(r * N), ndesc(ak + r * rstep, lbo, 128), bd, p.idesc, acc);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(empty(st));
+                    ++use;
+                }
+            }
+            if (ok) mma_commit(tfull(b));
+        }
+        if (!ok) atomicExch(p.err, 6);
+        if (issued) {
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+        (void)nchunks;
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------ epilogue --
+        const int q = warp & 3;
+        const int m = 32 * q + lane;
+        const bool leader = threadIdx.x == 64;
+        const int Wh = p.W >> 1, Hh = p.H >> 1;
+        const int step = p.pool_out ? 2 : 1;
+        int tcount = 0;
+        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
+            const int b = tcount & 1;
+            if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
+            named_sync(1, 128);
+            if (*flag) break;
+            tc_fence_after();
+            int n, x0, y0, px, py;
+            tile_of(t, n, x0, y0, px, py);
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * R * N);
+            for (int r = 0; r < R; r += step) {
+                int x[2], y[2];
+                bool valid[2];
+                for (int e = 0; e < step; ++e) {
+                    if (p.parity) {
+                        x[e] = 2 * (x0 + m) + px;
+                        y[e] = 2 * (y0 + r + e) + py;
+                        valid[e] = (x0 + m) < Wh && (y0 + r + e) < Hh;
+                    } else {
+                        x[e] = x0 + m;
+                        y[e] = y0 + r + e;
+                        valid[e] = x[e] < p.W && y[e] < p.H;
+                    }
+                }
+                float h[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[2][16];
+                    for (int e = 0; e < step; ++e) {
+                        tmem_ld16(trow + (uint32_t)((r + e) * N + c0), v[e]);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[e][j] = fmaxf(v[e][j] + __ldg(p.bias + c0 + j), 0.f);
+                    }
+                    if (p.head_out) {
+                        for (int o = 0; o < p.head_o; ++o) {
+                            float sacc = 0.f;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) sacc = fmaf(__ldg(p.head_w + o * N + c0 + j), v[0][j], sacc);
+                            h[o] += sacc;
+                        }
+                        continue;
+                    }
+                    for (int e = 0; e < step; ++e)
+                        if (valid[e]) st_bf16x16(p.out + (((size_t)n * p.H + y[e]) * p.W + x[e]) * N + c0, v[e]);
+                    if (step == 2) {
+                        float pm[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float a = fmaxf(v[0][j], v[1][j]);
+                            pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
+                        }
+                        if ((m & 1) == 0 && valid[0] && valid[1])
+                            st_bf16x16(p.pool_out + (((size_t)n * Hh + (y[0] >> 1)) * Wh + (x[0] >> 1)) * N + c0, pm);
+                    }
+                }
+                if (p.head_out && valid[0]) {
+                    const size_t pix = ((size_t)n * p.H + y[0]) * p.W + x[0];
+                    for (int o = 0; o < p.head_o; ++o)
+                        p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + __ldg(p.head_b + o))));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(b));
+        }
+        if (leader && *flag) atomicExch(p.err, 7);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
 // ------------------------------------------------------------------ host side ----
 
 CUtensorMapSwizzle swizzle_for(int kc) {
@@ -412,6 +708,8 @@ bool tc_available() { return true; }
 // padded to 16 so that every K chunk is one 32-byte MMA step).
 static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 16 : L.cin0; }
 
+static cudaError_t prepare_halo_weights(ConvLayer& L, int CK);
+
 cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p) {
     if (p != LNR_BF16) return cudaErrorNotSupported;
     const int c0 = tc_c0(L), cin = L.cin0 + L.cin1, cpad = c0 + L.cin1;
@@ -426,13 +724,15 @@ cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p) {
     L.wtc = nullptr;
     cudaError_t e = cudaMalloc(&L.wtc, w.size() * 2);
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(L.wtc, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(L.wtc, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    e = prepare_halo_weights(L, 16);
+    if (e != cudaSuccess) return e;
+    if (tc_c0(L) % 32 == 0 && L.cin1 % 32 == 0) e = prepare_halo_weights(L, 32);
+    return e;
 }
 
-void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
-             const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
-             cudaStream_t st) {
-    (void)prec;
+static void tc_init() {
     if (!g_num_sms) {
         int dev;
         cudaGetDevice(&dev);
@@ -440,7 +740,13 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
         cudaMalloc(&g_err, sizeof(int));
         cudaMemset(g_err, 0, sizeof(int));
         cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     }
+}
+
+static void tc_conv_generic(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
+                            const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
+                            cudaStream_t st) {
     Params p;
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout;
@@ -515,6 +821,153 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     const int grid = std::min(p.ntiles, g_num_sms);
     if (g_host_err || !L.wtc) return;
     k_conv_tc<<<grid, kThreads, smem, st>>>(p);
+}
+
+// ---- halo kernel host side ----
+
+static uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+// Weights of the halo kernel: [chunk][tap][CK/8][N][8] (chunk-major over the K segments),
+// i.e. the no-swizzle K-major core-matrix layout, one contiguous block per K chunk.
+static cudaError_t prepare_halo_weights(ConvLayer& L, int CK) {
+    void*& dst = (CK == 16) ? L.wh16 : L.wh32;
+    const int c0 = tc_c0(L), cin = L.cin0 + L.cin1, N = L.cout;
+    const int segC[2] = {c0, L.cin1}, segOff[2] = {0, c0};
+    const int nseg = L.cin1 ? 2 : 1;
+    for (int sg = 0; sg < nseg; ++sg)
+        if (segC[sg] % CK) return cudaErrorInvalidValue;
+    std::vector<__nv_bfloat16> w;
+    for (int sg = 0; sg < nseg; ++sg)
+        for (int cc = 0; cc < segC[sg] / CK; ++cc)
+            for (int t = 0; t < 9; ++t)
+                for (int j = 0; j < CK / 8; ++j)
+                    for (int n = 0; n < N; ++n)
+                        for (int e = 0; e < 8; ++e) {
+                            const int ch = segOff[sg] + cc * CK + 8 * j + e;  // padded channel
+                            int src = -1;                                     // original input channel
+                            if (ch < c0) src = ch < L.cin0 ? ch : -1;
+                            else src = L.cin0 + (ch - c0);
+                            const float v = src >= 0 ? L.wf[((size_t)n * cin + src) * 9 + t] : 0.f;
+                            w.push_back(__float2bfloat16(v));
+                        }
+    if (dst) cudaFree(dst);
+    dst = nullptr;
+    cudaError_t e = cudaMalloc(&dst, w.size() * 2);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(dst, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
+}
+
+static bool encode_nosw(CUtensorMap* m, int rank, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
+                        const cuuint32_t* box) {
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims, strides, box,
+                                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Default halo tile of a layer: R output rows (R*N accumulator columns, double-buffered in
+// the 512 TMEM columns; even when the layer pools) and K chunks of 16 channels.
+void halo_default(const ConvLayer& L, int& R, int& CK) {
+    const int N = L.cout;
+    if (L.cin1) R = std::min(2, 256 / N);
+    else R = std::min(8, 256 / N);
+    if (L.pool && (R & 1)) R = std::max(2, R - 1);
+    CK = 16;
+}
+
+bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
+                  const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
+                  int CK, cudaStream_t st) {
+    const void* wh = CK == 16 ? L.wh16 : L.wh32;
+    if (!wh) return false;
+    HParams p;
+    std::memset(&p, 0, sizeof(p));
+    const int N = L.cout, c0 = tc_c0(L);
+    if (2 * R * N > 512 || (L.pool && (R & 1))) return false;
+    p.N = N; p.W = W; p.H = H; p.B = B; p.R = R; p.CK = CK;
+    p.parity = L.cin1 > 0;
+    const cuuint64_t eb = 2;
+    int chunk = 0;
+    uint32_t a_region = 0;
+    auto set_seg = [&](HSeg& s, int kind, const void* src, int C, int Ws, int Hs) -> bool {
+        s.kind = kind;
+        s.rows = kind == 1 ? 2 * R + 1 : R + 2;
+        s.nchunk = C / CK;
+        s.chunk0 = chunk;
+        chunk += s.nchunk;
+        s.blk = align_up((uint32_t)s.rows * kHaloRowBytes, 128);
+        const uint32_t nblk = (uint32_t)(CK / 8) * (kind == 1 ? 2 : 1);
+        s.a_bytes = nblk * s.rows * kHaloRowBytes;
+        a_region = std::max(a_region, nblk * s.blk);
+        if (kind == 1) {
+            cuuint64_t dims[5] = {(cuuint64_t)C, 2, (cuuint64_t)Ws / 2, (cuuint64_t)Hs, (cuuint64_t)B};
+            cuuint64_t str[4] = {C * eb, 2 * C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
+            cuuint32_t box[5] = {8, 1, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
+            return encode_nosw(&s.a, 5, src, dims, str, box);
+        }
+        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
+        cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
+        cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
+        return encode_nosw(&s.a, 4, src, dims, str, box);
+    };
+    bool ok;
+    if (p.parity) {
+        p.nseg = 2;
+        ok = set_seg(p.seg[0], 1, src0, c0, W, H) && set_seg(p.seg[1], 2, src1, L.cin1, W / 2, H / 2);
+        p.tiles_x = (W / 2 + 127) / 128;
+        p.tiles_y = (H / 2 + R - 1) / R;
+        p.ntiles = B * 4 * p.tiles_y * p.tiles_x;
+    } else {
+        p.nseg = 1;
+        ok = set_seg(p.seg[0], 0, src0, c0, W, H);
+        p.tiles_x = (W + 127) / 128;
+        p.tiles_y = (H + R - 1) / R;
+        p.ntiles = B * p.tiles_y * p.tiles_x;
+    }
+    if (!ok) {
+        g_host_err = 4;
+        return true;
+    }
+    p.a_region = align_up(a_region, 1024);
+    p.b_bytes = (uint32_t)(9 * N * CK * 2);
+    p.stage_bytes = align_up(p.a_region + p.b_bytes, 1024);
+    p.stages = std::min<int>(8, (int)((220u * 1024u) / p.stage_bytes));
+    if (p.stages < 2) return false;
+    uint32_t cols = 32;
+    while (cols < 2u * R * N) cols <<= 1;
+    p.tmem_cols = cols;
+    p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    p.wB = static_cast<const __nv_bfloat16*>(wh);
+    p.bias = L.b32;
+    p.out = static_cast<__nv_bfloat16*>(out);
+    p.pool_out = static_cast<__nv_bfloat16*>(pool_out);
+    p.head_w = head_w;
+    p.head_b = head_b;
+    p.head_out = head_out;
+    p.head_o = head_o;
+    p.err = g_err;
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16;
+    const int grid = std::min(p.ntiles, g_num_sms);
+    k_conv_halo<<<grid, kThreads, smem, st>>>(p);
+    return true;
+}
+
+void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
+             const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
+             cudaStream_t st) {
+    (void)prec;
+    tc_init();
+    static const int forced = [] {
+        const char* e = getenv("LNR_CONV_KERNEL");
+        return (e && !strcmp(e, "generic")) ? 2 : 0;
+    }();
+    const int mode = forced ? forced : L.tc_mode;
+    if (mode != 2) {
+        int R = L.tc_R, CK = L.tc_CK;
+        if (mode == 0) halo_default(L, R, CK);
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, CK, st)) return;
+    }
+    tc_conv_generic(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, st);
 }
 
 int tc_error_word() {
