@@ -241,8 +241,8 @@ lnr_status lnr_destroy(lnr_ctx* c) {
         if (L.w32) cudaFree(L.w32);
         if (L.b32) cudaFree(L.b32);
         if (L.wtc) cudaFree(L.wtc);
-        if (L.wh16) cudaFree(L.wh16);
-        if (L.wh32) cudaFree(L.wh32);
+        for (void* w : L.wh)
+            if (w) cudaFree(w);
         if (L.wscale) cudaFree(L.wscale);
     }
     if (c->unet.head_w) cudaFree(c->unet.head_w);
@@ -349,8 +349,8 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
         if (Lr.w32) cudaFree(Lr.w32);
         if (Lr.b32) cudaFree(Lr.b32);
         if (Lr.wtc) cudaFree(Lr.wtc);
-        if (Lr.wh16) cudaFree(Lr.wh16);
-        if (Lr.wh32) cudaFree(Lr.wh32);
+        for (void* w : Lr.wh)
+            if (w) cudaFree(w);
         if (Lr.wscale) cudaFree(Lr.wscale);
     }
     Unet u;

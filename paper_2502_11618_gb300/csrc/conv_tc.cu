@@ -387,39 +387,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
 
 // ================================================================ halo kernel ==
 //
-// The same convolution with the input staged ONCE per tile: a tile is R output rows x 128
-// columns; for every K chunk of CK channels the producer loads the input halo (R+2 rows x
-// 130 columns, or the parity-class rows for the decoder's first conv) in the MMA's
-// no-swizzle K-major layout (8-channel blocks, 16 bytes per pixel, pixels at 16-byte
-// pitch), plus the chunk's weights for all 9 taps.  Every tap is then just a descriptor
-// offset into the staged halo (one pixel = 16 bytes, one row = 130 pixels), so the 9 taps
-// x R rows of MMAs read the halo that was fetched once.  The R accumulators of a tile sit
-// side by side in TMEM (R*N columns, double-buffered).
-// 2x2 pooling needs no shared-memory exchange: a thread owns one column of R rows, and
-// its horizontal neighbour is the adjacent lane.
+// The same convolution with the input staged ONCE per tile and K chunk: a tile is R output
+// rows x 128 columns (or, for the decoder's first conv, R coarse rows x 128 coarse columns
+// of one parity class).  For every K chunk of ck channels the producer loads the input
+// halo -- R+2 rows x 130 pixels (or the parity-class rows) -- with one TMA box whose
+// innermost extent is the whole chunk (32, 64 or 128 bytes per pixel, swizzled), plus the
+// chunk's weights for all 9 taps.  The tensor cores apply the swizzle from absolute
+// shared-memory address bits, as TMA does, so each tap is just the halo's start address
+// shifted by whole pixels and rows: the 9 taps x R rows of MMAs all read the halo that was
+// fetched once.  The R accumulators of a tile sit side by side in TMEM (R*N columns,
+// double-buffered).  2x2 pooling needs no shared-memory exchange: a thread owns one column
+// of R rows and its horizontal neighbour is the adjacent lane.
 
-constexpr int kHaloW = 130;                 // staged pixels per halo row
-constexpr uint32_t kHaloRowBytes = kHaloW * 16;
+constexpr int kHaloW = 130;  // staged pixels per halo row
 
 struct HSeg {
-    CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {8, 130, rows, 1}; kind 1: 5-D, box {8, 1, 130, rows, 1}
+    CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {ck, 130, rows, 1}; kind 1: 5-D, box {ck, 1, 130, rows, 1}
+    CUtensorMap b;   // 3-D {ck, N, 9 * chunks}, box {ck, N, 9}: weights [chunk][tap][N][ck]
     int kind;        // 0: same-resolution source; 1: skip (parity tiles); 2: coarse (parity tiles)
-    int rows;        // halo rows staged per 8-channel block
+    int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel
+    int rows;        // halo rows staged
     int nchunk;      // K chunks of this segment
-    int chunk0;      // global index of its first chunk (weights are stored chunk-major)
-    uint32_t blk;    // bytes of one staged 8-channel block (128-byte aligned)
-    uint32_t a_bytes;
+    uint32_t pitch;  // bytes per staged pixel (= ck * 2)
+    uint32_t plane;  // bytes of one staged plane (rows x 130 pixels, 1024-aligned)
+    uint32_t a_bytes, b_off, bytes;  // A bytes per chunk, B offset in the stage, A + B bytes
+    uint32_t swz;    // UMMA layout type (SW128 = 2, SW64 = 4, SW32 = 6)
 };
 
 struct HParams {
     HSeg seg[2];
     int nseg;
-    int CK, R, parity, W, H, B, N;
+    int R, parity, W, H, B, N;
     int tiles_x, tiles_y, ntiles;
-    const __nv_bfloat16* wB;   // [chunk][tap][CK/8][N][8]
-    uint32_t b_bytes;          // 9 * N * CK * 2
     int stages;
-    uint32_t stage_bytes, a_region, tmem_cols, idesc;
+    uint32_t stage_bytes, tmem_cols, idesc;
     const float* bias;
     __nv_bfloat16* out;
     __nv_bfloat16* pool_out;
@@ -430,17 +431,11 @@ struct HParams {
     int* err;
 };
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// UMMA descriptor of a no-swizzle K-major tile: 8-row x 16-byte core matrices, LBO between
-// K-adjacent core matrices, SBO between 8-row groups.
-__device__ __forceinline__ uint64_t ndesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
@@ -470,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int R = p.R, N = p.N, CK = p.CK;
+    const int R = p.R, N = p.N;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
@@ -489,7 +484,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
-    const int nchunks = p.seg[0].nchunk + (p.nseg > 1 ? p.seg[1].nchunk : 0);
 
     auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
         const int tx = t % p.tiles_x;
@@ -521,19 +515,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     const int st = use % S;
                     if (!mbar_wait(empty(st), ((use / S) & 1) ^ 1)) { ok = false; break; }
                     const uint32_t a_dst = base + st * p.stage_bytes;
-                    mbar_expect_tx(full(st), s.a_bytes + p.b_bytes);
-                    for (int j = 0; j < CK / 8; ++j) {
-                        const int c8 = cc * CK + 8 * j;
-                        if (s.kind == 0) {
-                            tma_4d(a_dst + j * s.blk, &s.a, full(st), c8, x0 - 1, y0 - 1, n);
-                        } else if (s.kind == 2) {
-                            tma_4d(a_dst + j * s.blk, &s.a, full(st), c8, x0 - 1, y0 - 1, n);
-                        } else {
-                            for (int sx = 0; sx < 2; ++sx)
-                                tma_5d(a_dst + (2 * j + sx) * s.blk, &s.a, full(st), c8, sx, x0 - 1, 2 * y0 + py - 1, n);
-                        }
+                    mbar_expect_tx(full(st), s.bytes);
+                    const int c = cc * s.ck;
+                    if (s.kind == 1) {
+                        tma_5d(a_dst, &s.a, full(st), c, 0, x0 - 1, 2 * y0 + py - 1, n);
+                        tma_5d(a_dst + s.plane, &s.a, full(st), c, 1, x0 - 1, 2 * y0 + py - 1, n);
+                    } else {
+                        tma_4d(a_dst, &s.a, full(st), c, x0 - 1, y0 - 1, n);
                     }
-                    bulk_g2s(a_dst + p.a_region, p.wB + (size_t)(s.chunk0 + cc) * (p.b_bytes / 2), p.b_bytes, full(st));
+                    tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, cc * 9);
                     ++use;
                 }
             }
@@ -544,7 +534,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         // ----------------------------------------------------------------- MMA --
         int use = 0, tcount = 0;
         bool ok = true, issued = false;
-        const uint32_t bsbo = 128, blbo = (uint32_t)N * 16;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
             tile_of(t, n, x0, y0, px, py);
@@ -552,39 +541,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d0 = tmem + (uint32_t)(b * R * N);
-            int kc_global = 0;
+            bool first = true;
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
-                for (int cc = 0; cc < s.nchunk; ++cc, ++kc_global) {
+                const uint32_t pitch = s.pitch, rowb = kHaloW * pitch, sbo = 8 * pitch;
+                for (int cc = 0; cc < s.nchunk; ++cc) {
                     const int st = use % S;
                     if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_base = base + st * p.stage_bytes, b_base = a_base + p.a_region;
+                    const uint32_t a_base = base + st * p.stage_bytes, b_base = a_base + s.b_off;
                     for (int tap = 0; tap < 9; ++tap) {
                         const int ky = tap / 3, kx = tap % 3;
-                        // halo offset of this tap for output row 0, and the K-pair stride (LBO)
-                        uint32_t off, lbo, rstep;
+                        uint32_t off, rstep;  // halo offset of this tap at output row 0, row step
                         if (s.kind == 0) {
-                            off = ky * kHaloRowBytes + kx * 16;
-                            lbo = s.blk;
-                            rstep = kHaloRowBytes;
+                            off = ky * rowb + kx * pitch;
+                            rstep = rowb;
                         } else if (s.kind == 2) {
                             const int dx = (px + kx - 1) >> 1, dy = (py + ky - 1) >> 1;
-                            off = (1 + dy) * kHaloRowBytes + (1 + dx) * 16;
-                            lbo = s.blk;
-                            rstep = kHaloRowBytes;
+                            off = (1 + dy) * rowb + (1 + dx) * pitch;
+                            rstep = rowb;
                         } else {
                             const int dxf = px + kx - 1;
-                            off = (dxf & 1) * s.blk + ky * kHaloRowBytes + (1 + (dxf >> 1)) * 16;
-                            lbo = 2 * s.blk;
-                            rstep = 2 * kHaloRowBytes;
+                            off = (dxf & 1) * s.plane + ky * rowb + (1 + (dxf >> 1)) * pitch;
+                            rstep = 2 * rowb;
                         }
-                        for (int k16 = 0; k16 < CK / 16; ++k16) {
-                            const uint64_t bd = ndesc(b_base + (uint32_t)((tap * (CK / 8) + 2 * k16) * N * 16), blbo, bsbo);
-                            const uint32_t ak = a_base + 2 * k16 * lbo + off;
-                            const uint32_t acc = (kc_global | tap | k16) ? 1u : 0u;
+                        for (int k16 = 0; k16 < s.ck / 16; ++k16) {
+                            const uint64_t bd = sdesc(b_base + (uint32_t)(tap * N) * pitch + 32u * k16, sbo, s.swz);
+                            const uint32_t acc = first ? 0u : 1u;
                             for (int r = 0; r < R; ++r)
-                                mma_bf16(d0 + (uint32_t)(r * N), ndesc(ak + r * rstep, lbo, 128), bd, p.idesc, acc);
+                                mma_bf16(d0 + (uint32_t)(r * N), sdesc(a_base + off + r * rstep + 32u * k16, sbo, s.swz), bd,
+                                         p.idesc, acc);
+                            first = false;
                         }
                     }
                     issued = true;
@@ -599,7 +586,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             mma_commit(drain);
             mbar_wait(drain, 0);
         }
-        (void)nchunks;
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
@@ -726,10 +712,11 @@ cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p) {
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(L.wtc, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    e = prepare_halo_weights(L, 16);
-    if (e != cudaSuccess) return e;
-    if (tc_c0(L) % 32 == 0 && L.cin1 % 32 == 0) e = prepare_halo_weights(L, 32);
-    return e;
+    for (int ck : {16, 32, 64}) {
+        e = prepare_halo_weights(L, ck);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static void tc_init() {
@@ -826,30 +813,32 @@ static void tc_conv_generic(const ConvLayer& L, const void* src0, const void* sr
 // ---- halo kernel host side ----
 
 static uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 
-// Weights of the halo kernel: [chunk][tap][CK/8][N][8] (chunk-major over the K segments),
-// i.e. the no-swizzle K-major core-matrix layout, one contiguous block per K chunk.
-static cudaError_t prepare_halo_weights(ConvLayer& L, int CK) {
-    void*& dst = (CK == 16) ? L.wh16 : L.wh32;
+// Weights of the halo kernel for chunks of at most ckmax channels: every K segment's
+// chunks in turn, each chunk [tap][N][ck] with ck = min(C_segment, ckmax) -- one TMA box
+// {ck, N, 9} per chunk, swizzled like the halo rows.
+static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
+    void*& dst = L.wh[ck_index(ckmax)];
     const int c0 = tc_c0(L), cin = L.cin0 + L.cin1, N = L.cout;
     const int segC[2] = {c0, L.cin1}, segOff[2] = {0, c0};
     const int nseg = L.cin1 ? 2 : 1;
-    for (int sg = 0; sg < nseg; ++sg)
-        if (segC[sg] % CK) return cudaErrorInvalidValue;
     std::vector<__nv_bfloat16> w;
-    for (int sg = 0; sg < nseg; ++sg)
-        for (int cc = 0; cc < segC[sg] / CK; ++cc)
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int ck = std::min(segC[sg], ckmax);
+        if (segC[sg] % ck) return cudaErrorInvalidValue;
+        for (int cc = 0; cc < segC[sg] / ck; ++cc)
             for (int t = 0; t < 9; ++t)
-                for (int j = 0; j < CK / 8; ++j)
-                    for (int n = 0; n < N; ++n)
-                        for (int e = 0; e < 8; ++e) {
-                            const int ch = segOff[sg] + cc * CK + 8 * j + e;  // padded channel
-                            int src = -1;                                     // original input channel
-                            if (ch < c0) src = ch < L.cin0 ? ch : -1;
-                            else src = L.cin0 + (ch - c0);
-                            const float v = src >= 0 ? L.wf[((size_t)n * cin + src) * 9 + t] : 0.f;
-                            w.push_back(__float2bfloat16(v));
-                        }
+                for (int n = 0; n < N; ++n)
+                    for (int e = 0; e < ck; ++e) {
+                        const int ch = segOff[sg] + cc * ck + e;  // padded channel
+                        int src;
+                        if (ch < c0) src = ch < L.cin0 ? ch : -1;
+                        else src = L.cin0 + (ch - c0);
+                        const float v = src >= 0 ? L.wf[((size_t)n * cin + src) * 9 + t] : 0.f;
+                        w.push_back(__float2bfloat16(v));
+                    }
+    }
     if (dst) cudaFree(dst);
     dst = nullptr;
     cudaError_t e = cudaMalloc(&dst, w.size() * 2);
@@ -857,63 +846,103 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int CK) {
     return cudaMemcpy(dst, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
 }
 
-static bool encode_nosw(CUtensorMap* m, int rank, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
-                        const cuuint32_t* box) {
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    return cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims, strides, box,
-                                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+// Bytes of one pipeline stage of the halo kernel for a layer at tile height R and chunks
+// of at most ckmax channels (the larger of its K segments).
+static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int ckmax) {
+    const int segC[2] = {tc_c0(L), L.cin1};
+    uint32_t st = 0;
+    for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg) {
+        const int ck = std::min(segC[sg], ckmax);
+        const int kind1 = L.cin1 && sg == 0;
+        const uint32_t rows = kind1 ? 2 * R + 1 : R + 2, pitch = 2 * ck;
+        const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
+        st = std::max(st, align_up((kind1 ? 2 : 1) * plane + 9u * L.cout * pitch, 1024));
+    }
+    return st;
 }
 
-// Default halo tile of a layer: R output rows (R*N accumulator columns, double-buffered in
-// the 512 TMEM columns; even when the layer pools) and K chunks of 16 channels.
-void halo_default(const ConvLayer& L, int& R, int& CK) {
+// Default halo tile of a layer: the tallest tile whose R*N accumulator columns fit TMEM
+// twice (even R when the layer pools), then the widest chunk (64, then 32 channels) that
+// leaves at least two pipeline stages; 16-channel chunks only as a last resort.
+void halo_default(const ConvLayer& L, int& R, int& ckmax) {
     const int N = L.cout;
-    if (L.cin1) R = std::min(2, 256 / N);
-    else R = std::min(8, 256 / N);
-    if (L.pool && (R & 1)) R = std::max(2, R - 1);
-    CK = 16;
+    int rmax = std::min(8, 256 / N);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int r = rmax; r >= 1; r = r > 1 ? r / 2 : 0) {
+            if (L.pool && (r & 1)) continue;
+            const int cks[2] = {64, 32};
+            for (int i = 0; i < (pass ? 1 : 2); ++i) {
+                const int ck = pass ? 16 : cks[i];
+                if (halo_stage_bytes(L, r, ck) * 2 <= 220u * 1024u) {
+                    R = r;
+                    ckmax = ck;
+                    return;
+                }
+            }
+        }
+    R = 1;
+    ckmax = 16;
 }
 
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
-                  int CK, cudaStream_t st) {
-    const void* wh = CK == 16 ? L.wh16 : L.wh32;
+                  int ckmax, cudaStream_t st) {
+    const __nv_bfloat16* wh = static_cast<const __nv_bfloat16*>(L.wh[ck_index(ckmax)]);
     if (!wh) return false;
     HParams p;
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout, c0 = tc_c0(L);
-    if (2 * R * N > 512 || (L.pool && (R & 1))) return false;
-    p.N = N; p.W = W; p.H = H; p.B = B; p.R = R; p.CK = CK;
+    if (R < 1 || 2 * R * N > 512 || (L.pool && (R & 1))) return false;
+    p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = L.cin1 > 0;
     const cuuint64_t eb = 2;
-    int chunk = 0;
-    uint32_t a_region = 0;
+    size_t w_off = 0;  // elements into wh
+    uint32_t stage = 0;
     auto set_seg = [&](HSeg& s, int kind, const void* src, int C, int Ws, int Hs) -> bool {
         s.kind = kind;
+        s.ck = std::min(C, ckmax);
+        s.pitch = (uint32_t)s.ck * 2;
+        s.swz = umma_layout_for(s.ck);
         s.rows = kind == 1 ? 2 * R + 1 : R + 2;
-        s.nchunk = C / CK;
-        s.chunk0 = chunk;
-        chunk += s.nchunk;
-        s.blk = align_up((uint32_t)s.rows * kHaloRowBytes, 128);
-        const uint32_t nblk = (uint32_t)(CK / 8) * (kind == 1 ? 2 : 1);
-        s.a_bytes = nblk * s.rows * kHaloRowBytes;
-        a_region = std::max(a_region, nblk * s.blk);
+        s.nchunk = C / s.ck;
+        const uint32_t planes = kind == 1 ? 2 : 1;
+        s.plane = align_up((uint32_t)s.rows * kHaloW * s.pitch, 1024);
+        s.a_bytes = planes * (uint32_t)s.rows * kHaloW * s.pitch;
+        s.b_off = planes * s.plane;
+        const uint32_t b_bytes = 9u * N * s.pitch;
+        s.bytes = s.a_bytes + b_bytes;
+        stage = std::max(stage, align_up(s.b_off + b_bytes, 1024));
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        bool ok;
         if (kind == 1) {
             cuuint64_t dims[5] = {(cuuint64_t)C, 2, (cuuint64_t)Ws / 2, (cuuint64_t)Hs, (cuuint64_t)B};
             cuuint64_t str[4] = {C * eb, 2 * C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
-            cuuint32_t box[5] = {8, 1, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-            return encode_nosw(&s.a, 5, src, dims, str, box);
+            cuuint32_t box[5] = {(cuuint32_t)s.ck, 1, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
+            ok = cuTensorMapEncodeTiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(src), dims, str, box, es,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        } else {
+            cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
+            cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
+            cuuint32_t box[4] = {(cuuint32_t)s.ck, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
+            ok = cuTensorMapEncodeTiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(src), dims, str, box, es,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
-        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
-        cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
-        cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-        return encode_nosw(&s.a, 4, src, dims, str, box);
+        cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)9 * s.nchunk};
+        cuuint64_t wstr[2] = {s.ck * eb, (cuuint64_t)N * s.ck * eb};
+        cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, 9};
+        ok = ok && cuTensorMapEncodeTiled(&s.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(wh + w_off),
+                                          wd, wstr, wbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck),
+                                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        w_off += (size_t)s.nchunk * 9 * N * s.ck;
+        return ok;
     };
     bool ok;
     if (p.parity) {
         p.nseg = 2;
-        ok = set_seg(p.seg[0], 1, src0, c0, W, H) && set_seg(p.seg[1], 2, src1, L.cin1, W / 2, H / 2);
+        ok = set_seg(p.seg[0], 1, src0, c0, W, H);
+        ok = set_seg(p.seg[1], 2, src1, L.cin1, W / 2, H / 2) && ok;
         p.tiles_x = (W / 2 + 127) / 128;
         p.tiles_y = (H / 2 + R - 1) / R;
         p.ntiles = B * 4 * p.tiles_y * p.tiles_x;
@@ -924,20 +953,17 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.tiles_y = (H + R - 1) / R;
         p.ntiles = B * p.tiles_y * p.tiles_x;
     }
+    p.stage_bytes = stage;
+    p.stages = std::min<int>(8, (int)((220u * 1024u) / p.stage_bytes));
+    if (p.stages < 2) return false;
     if (!ok) {
         g_host_err = 4;
         return true;
     }
-    p.a_region = align_up(a_region, 1024);
-    p.b_bytes = (uint32_t)(9 * N * CK * 2);
-    p.stage_bytes = align_up(p.a_region + p.b_bytes, 1024);
-    p.stages = std::min<int>(8, (int)((220u * 1024u) / p.stage_bytes));
-    if (p.stages < 2) return false;
     uint32_t cols = 32;
     while (cols < 2u * R * N) cols <<= 1;
     p.tmem_cols = cols;
     p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    p.wB = static_cast<const __nv_bfloat16*>(wh);
     p.bias = L.b32;
     p.out = static_cast<__nv_bfloat16*>(out);
     p.pool_out = static_cast<__nv_bfloat16*>(pool_out);

@@ -45,8 +45,7 @@ struct ConvLayer {
     float* w32 = nullptr;   // device, FP32 [tap][cin_pad][cout]
     float* b32 = nullptr;   // device, FP32 [cout]
     void* wtc = nullptr;    // device, tensor-core weights [cout][tap][cin_pad] (bf16 or fp8)
-    void* wh16 = nullptr;   // device, halo-kernel weights, K chunks of 16 channels
-    void* wh32 = nullptr;   // device, halo-kernel weights, K chunks of 32 channels
+    void* wh[3] = {nullptr, nullptr, nullptr};  // device, halo-kernel weights for chunks of <= 16 / 32 / 64 channels
     int tc_mode = 0;        // 0: halo kernel, default tile; 1: halo kernel, tc_R x tc_CK; 2: generic kernel
     int tc_R = 0, tc_CK = 0;
     float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null

@@ -91,3 +91,40 @@ def test_bf16_batch_equals_single_and_precision_switch(lnr, room):
     ref = oracle.render(g, views[0], intr, W, H, 3, 1.0, w, ch)
     assert np.abs(y32 - ref["y"]).max() <= 1e-4
     r.close()
+
+
+_KERNEL_SCRIPT = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import synth, oracle
+import paper_2502_11618_gb300 as lnr
+s = synth.multiroom_scene(n_points=300_000)
+g = oracle.build_grid(s.xyz, s.rgb, s.scan_id, 0.25)
+ch = (32, 64, 128, 256)
+w = synth.unet_weights(ch, seed=3)
+r = lnr.Renderer(0); r.load_cloud(s.xyz, s.rgb, s.scan_id); r.build_grid(0.25); r.set_unet(ch, w, "bf16")
+W, H = 264, 136
+intr = synth.intrinsics_for(W, H)
+worst = 0.0
+for v in synth.random_poses(s, 2, seed=7):
+    ref = oracle.render(g, v, intr, W, H, 4, 1.0, w, ch)
+    y = r.render(v, intr, W, H, 4, 1.0)
+    mse = float(np.mean((y - ref["y"]) ** 2))
+    worst = max(worst, float(np.abs(y - ref["y"]).max()))
+    assert 10 * np.log10(1 / mse) >= 45.0
+print("maxabs", worst)
+assert worst <= 2e-2
+"""
+
+
+@pytest.mark.parametrize("kernel", ["generic", "halo"])
+def test_bf16_each_conv_kernel(lnr, kernel):
+    """Both tensor-core conv kernels (forced for every layer) meet the BF16 bars."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, LNR_CONV_KERNEL=kernel)
+    r = subprocess.run([sys.executable, "-c", _KERNEL_SCRIPT.format(root=root)], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
