@@ -668,6 +668,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
 
 // ------------------------------------------------------------------ host side ----
 
+// Chunk width of a K segment of C channels (C a multiple of 16): the largest of 64, 32, 16
+// that is at most ckmax and divides C.
+int seg_ck(int C, int ckmax) {
+    int ck = std::min(C, ckmax);
+    while (C % ck) ck >>= 1;
+    return ck;
+}
+
 CUtensorMapSwizzle swizzle_for(int kc) {
     return kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
 }
@@ -747,7 +755,7 @@ static void tc_conv_generic(const ConvLayer& L, const void* src0, const void* sr
     const cuuint64_t Ktot = 9ull * cpad;
     auto set_seg = [&](Seg& s, int kind, const void* src, int C, int koff, int Ws, int Hs) {
         s.kind = kind;
-        s.kc = C >= 64 ? 64 : C;
+        s.kc = seg_ck(C, 64);
         s.nchunk = C / s.kc;
         s.koff = koff;
         s.swz = umma_layout_for(s.kc);
@@ -815,6 +823,7 @@ static void tc_conv_generic(const ConvLayer& L, const void* src0, const void* sr
 static uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 
+
 // Weights of the halo kernel for chunks of at most ckmax channels: every K segment's
 // chunks in turn, each chunk [tap][N][ck] with ck = min(C_segment, ckmax) -- one TMA box
 // {ck, N, 9} per chunk, swizzled like the halo rows.
@@ -825,8 +834,7 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
     const int nseg = L.cin1 ? 2 : 1;
     std::vector<__nv_bfloat16> w;
     for (int sg = 0; sg < nseg; ++sg) {
-        const int ck = std::min(segC[sg], ckmax);
-        if (segC[sg] % ck) return cudaErrorInvalidValue;
+        const int ck = seg_ck(segC[sg], ckmax);
         for (int cc = 0; cc < segC[sg] / ck; ++cc)
             for (int t = 0; t < 9; ++t)
                 for (int n = 0; n < N; ++n)
@@ -852,7 +860,7 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int ckmax) {
     const int segC[2] = {tc_c0(L), L.cin1};
     uint32_t st = 0;
     for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg) {
-        const int ck = std::min(segC[sg], ckmax);
+        const int ck = seg_ck(segC[sg], ckmax);
         const int kind1 = L.cin1 && sg == 0;
         const uint32_t rows = kind1 ? 2 * R + 1 : R + 2, pitch = 2 * ck;
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
@@ -900,7 +908,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     uint32_t stage = 0;
     auto set_seg = [&](HSeg& s, int kind, const void* src, int C, int Ws, int Hs) -> bool {
         s.kind = kind;
-        s.ck = std::min(C, ckmax);
+        s.ck = seg_ck(C, ckmax);
         s.pitch = (uint32_t)s.ck * 2;
         s.swz = umma_layout_for(s.ck);
         s.rows = kind == 1 ? 2 * R + 1 : R + 2;
