@@ -450,6 +450,30 @@ __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
     reinterpret_cast<uint4*>(dst)[1] = pk[1];
 }
 
+// 16 TMEM columns of this warp's lanes into r without waiting; tmem_wait16 completes it.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// Waits for every TMEM load this thread issued; r is threaded through so that no use of
+// it can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// High bits of a swizzled K-major UMMA descriptor (everything but the start address).
+__device__ __forceinline__ uint64_t sdesc_hi(uint32_t sbo, uint32_t swz) {
+    return ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swz << 61);
+}
+
+template <int R, bool PAR>
 __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -464,8 +488,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     const uint32_t drain = bars + 8u * (2 * S + 4);
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
+    float* sbias = reinterpret_cast<float*>(gbase + (tslot - base) + 16);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int R = p.R, N = p.N;
+    const int N = p.N;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
@@ -479,27 +504,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         *flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = threadIdx.x; i < N; i += kThreads) sbias[i] = p.bias[i];
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
 
+    // tile t -> image n, first column x0 and first row y0 (coarse for parity tiles) and the
+    // parity class (px, py); parity is the fastest index so that the four classes of a
+    // region run back to back and share its halo in L2
     auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
-        const int tx = t % p.tiles_x;
-        int r = t / p.tiles_x;
-        const int ty = r % p.tiles_y;
-        r /= p.tiles_y;
-        if (p.parity) {
-            px = r & 1;
-            py = (r >> 1) & 1;
-            n = r >> 2;
+        if (PAR) {
+            px = t & 1;
+            py = (t >> 1) & 1;
+            t >>= 2;
         } else {
             px = py = 0;
-            n = r;
         }
-        x0 = tx * 128;   // first (coarse, for parity tiles) column
-        y0 = ty * R;     // first (coarse, for parity tiles) row
+        const int tx = t % p.tiles_x;
+        t /= p.tiles_x;
+        const int ty = t % p.tiles_y;
+        n = t / p.tiles_y;
+        x0 = tx * 128;
+        y0 = ty * R;
     };
 
     if (warp == 0 && lane == 0) {
@@ -517,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     const uint32_t a_dst = base + st * p.stage_bytes;
                     mbar_expect_tx(full(st), s.bytes);
                     const int c = cc * s.ck;
-                    if (s.kind == 1) {
+                    if (PAR && sg == 0) {
                         tma_5d(a_dst, &s.a, full(st), c, 0, x0 - 1, 2 * y0 + py - 1, n);
                         tma_5d(a_dst + s.plane, &s.a, full(st), c, 1, x0 - 1, 2 * y0 + py - 1, n);
                     } else {
@@ -532,6 +560,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
     } else if (warp == 1 && lane == 0) {
         // ----------------------------------------------------------------- MMA --
+        // Descriptors are built once per stage; every tap, row and K step only adds a
+        // constant to the start-address field (address >> 4, 14 bits).
         int use = 0, tcount = 0;
         bool ok = true, issued = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
@@ -541,37 +571,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d0 = tmem + (uint32_t)(b * R * N);
-            bool first = true;
+            uint32_t first = 1;
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
-                const uint32_t pitch = s.pitch, rowb = kHaloW * pitch, sbo = 8 * pitch;
+                const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16;
+                const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
+                const int nk = s.ck >> 4;
+                const bool skip = PAR && sg == 0, coarse = PAR && sg == 1;
+                // per-tap offset (16-byte units) of output row 0, and the row step
+                uint32_t off[9];
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap % 3;
+                    if (skip) {
+                        const int dxf = px + kx - 1;
+                        off[tap] = (uint32_t)(dxf & 1) * (s.plane >> 4) + ky * row16 + (uint32_t)(1 + (dxf >> 1)) * pitch16;
+                    } else if (coarse) {
+                        off[tap] = (uint32_t)(1 + ((py + ky - 1) >> 1)) * row16 + (uint32_t)(1 + ((px + kx - 1) >> 1)) * pitch16;
+                    } else {
+                        off[tap] = ky * row16 + kx * pitch16;
+                    }
+                }
+                const uint32_t rstep = skip ? 2 * row16 : row16;
+                const uint32_t btap = (uint32_t)N * pitch16;
                 for (int cc = 0; cc < s.nchunk; ++cc) {
                     const int st = use % S;
                     if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_base = base + st * p.stage_bytes, b_base = a_base + s.b_off;
+                    const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
+                    const uint32_t b0 = a0 + (s.b_off >> 4);
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
-                        const int ky = tap / 3, kx = tap % 3;
-                        uint32_t off, rstep;  // halo offset of this tap at output row 0, row step
-                        if (s.kind == 0) {
-                            off = ky * rowb + kx * pitch;
-                            rstep = rowb;
-                        } else if (s.kind == 2) {
-                            const int dx = (px + kx - 1) >> 1, dy = (py + ky - 1) >> 1;
-                            off = (1 + dy) * rowb + (1 + dx) * pitch;
-                            rstep = rowb;
-                        } else {
-                            const int dxf = px + kx - 1;
-                            off = (dxf & 1) * s.plane + ky * rowb + (1 + (dxf >> 1)) * pitch;
-                            rstep = 2 * rowb;
-                        }
-                        for (int k16 = 0; k16 < s.ck / 16; ++k16) {
-                            const uint64_t bd = sdesc(b_base + (uint32_t)(tap * N) * pitch + 32u * k16, sbo, s.swz);
+                        for (int k = 0; k < nk; ++k) {
+                            const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
+                            const uint32_t ab = a0 + off[tap] + 2 * k;
                             const uint32_t acc = first ? 0u : 1u;
+#pragma unroll
                             for (int r = 0; r < R; ++r)
-                                mma_bf16(d0 + (uint32_t)(r * N), sdesc(a_base + off + r * rstep + 32u * k16, sbo, s.swz), bd,
-                                         p.idesc, acc);
-                            first = false;
+                                mma_bf16(d0 + (uint32_t)(r * N), hi | (uint64_t)(ab + r * rstep), bd, p.idesc, acc);
+                            first = 0;
                         }
                     }
                     issued = true;
@@ -592,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         const int m = 32 * q + lane;
         const bool leader = threadIdx.x == 64;
         const int Wh = p.W >> 1, Hh = p.H >> 1;
-        const int step = p.pool_out ? 2 : 1;
+        const bool pool = p.pool_out != nullptr;
         int tcount = 0;
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
             const int b = tcount & 1;
@@ -603,54 +641,79 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             int n, x0, y0, px, py;
             tile_of(t, n, x0, y0, px, py);
             const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * R * N);
-            for (int r = 0; r < R; r += step) {
-                int x[2], y[2];
-                bool valid[2];
-                for (int e = 0; e < step; ++e) {
-                    if (p.parity) {
-                        x[e] = 2 * (x0 + m) + px;
-                        y[e] = 2 * (y0 + r + e) + py;
-                        valid[e] = (x0 + m) < Wh && (y0 + r + e) < Hh;
-                    } else {
-                        x[e] = x0 + m;
-                        y[e] = y0 + r + e;
-                        valid[e] = x[e] < p.W && y[e] < p.H;
-                    }
-                }
-                float h[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    float v[2][16];
-                    for (int e = 0; e < step; ++e) {
-                        tmem_ld16(trow + (uint32_t)((r + e) * N + c0), v[e]);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[e][j] = fmaxf(v[e][j] + __ldg(p.bias + c0 + j), 0.f);
-                    }
-                    if (p.head_out) {
-                        for (int o = 0; o < p.head_o; ++o) {
-                            float sacc = 0.f;
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) sacc = fmaf(__ldg(p.head_w + o * N + c0 + j), v[0][j], sacc);
-                            h[o] += sacc;
-                        }
-                        continue;
-                    }
-                    for (int e = 0; e < step; ++e)
-                        if (valid[e]) st_bf16x16(p.out + (((size_t)n * p.H + y[e]) * p.W + x[e]) * N + c0, v[e]);
-                    if (step == 2) {
-                        float pm[16];
+            if (pool) {
+                // rows in pairs: both rows stored, their 2x2 maximum pooled with the lane
+                // that holds the neighbouring column
+                for (int r = 0; r < R; r += 2) {
+                    const int x = x0 + m, y = y0 + r;
+                    const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        uint32_t u0[16], u1[16];
+                        tmem_ld16_async(trow + (uint32_t)(r * N + c0), u0);
+                        tmem_ld16_async(trow + (uint32_t)((r + 1) * N + c0), u1);
+                        tmem_wait16(u0);
+                        tmem_wait16(u1);
+                        float f0[16], f1[16], pm[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float a = fmaxf(v[0][j], v[1][j]);
+                            const float bj = sbias[c0 + j];
+                            f0[j] = fmaxf(__uint_as_float(u0[j]) + bj, 0.f);
+                            f1[j] = fmaxf(__uint_as_float(u1[j]) + bj, 0.f);
+                            const float a = fmaxf(f0[j], f1[j]);
                             pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                         }
-                        if ((m & 1) == 0 && valid[0] && valid[1])
-                            st_bf16x16(p.pool_out + (((size_t)n * Hh + (y[0] >> 1)) * Wh + (x[0] >> 1)) * N + c0, pm);
+                        if (v0) st_bf16x16(p.out + (((size_t)n * p.H + y) * p.W + x) * N + c0, f0);
+                        if (v1) st_bf16x16(p.out + (((size_t)n * p.H + y + 1) * p.W + x) * N + c0, f1);
+                        if ((m & 1) == 0 && v1)
+                            st_bf16x16(p.pool_out + (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N + c0, pm);
                     }
                 }
-                if (p.head_out && valid[0]) {
-                    const size_t pix = ((size_t)n * p.H + y[0]) * p.W + x[0];
-                    for (int o = 0; o < p.head_o; ++o)
-                        p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + __ldg(p.head_b + o))));
+            } else {
+                for (int r = 0; r < R; ++r) {
+                    int x, y;
+                    bool v;
+                    if (PAR) {
+                        x = 2 * (x0 + m) + px;
+                        y = 2 * (y0 + r) + py;
+                        v = (x0 + m) < Wh && (y0 + r) < Hh;
+                    } else {
+                        x = x0 + m;
+                        y = y0 + r;
+                        v = x < p.W && y < p.H;
+                    }
+                    const size_t pix = ((size_t)n * p.H + y) * p.W + x;
+                    float h[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t u0[16], u1[16];
+                        const bool two = c0 + 16 < N;
+                        tmem_ld16_async(trow + (uint32_t)(r * N + c0), u0);
+                        if (two) tmem_ld16_async(trow + (uint32_t)(r * N + c0 + 16), u1);
+                        tmem_wait16(u0);
+                        if (two) tmem_wait16(u1);
+                        float f0[16], f1[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            f0[j] = fmaxf(__uint_as_float(u0[j]) + sbias[c0 + j], 0.f);
+                            f1[j] = two ? fmaxf(__uint_as_float(u1[j]) + sbias[c0 + 16 + j], 0.f) : 0.f;
+                        }
+                        if (p.head_out) {
+                            for (int o = 0; o < p.head_o; ++o) {
+                                float sacc = 0.f;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    sacc = fmaf(__ldg(p.head_w + o * N + c0 + j), f0[j], sacc);
+                                    if (two) sacc = fmaf(__ldg(p.head_w + o * N + c0 + 16 + j), f1[j], sacc);
+                                }
+                                h[o] += sacc;
+                            }
+                        } else if (v) {
+                            st_bf16x16(p.out + pix * N + c0, f0);
+                            if (two) st_bf16x16(p.out + pix * N + c0 + 16, f1);
+                        }
+                    }
+                    if (p.head_out && v)
+                        for (int o = 0; o < p.head_o; ++o)
+                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + __ldg(p.head_b + o))));
                 }
             }
             tc_fence_before();
@@ -735,7 +798,6 @@ static void tc_init() {
         cudaMalloc(&g_err, sizeof(int));
         cudaMemset(g_err, 0, sizeof(int));
         cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     }
 }
 
@@ -900,7 +962,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     HParams p;
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout, c0 = tc_c0(L);
-    if (R < 1 || 2 * R * N > 512 || (L.pool && (R & 1))) return false;
+    if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = L.cin1 > 0;
     const cuuint64_t eb = 2;
@@ -980,9 +1042,31 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
-    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16;
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 + 4 * (size_t)N;
     const int grid = std::min(p.ntiles, g_num_sms);
-    k_conv_halo<<<grid, kThreads, smem, st>>>(p);
+    auto launch = [&](auto kern) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr = true;
+        }
+        kern<<<grid, kThreads, smem, st>>>(p);
+    };
+    if (p.parity) {
+        switch (R) {
+            case 1: launch(k_conv_halo<1, true>); break;
+            case 2: launch(k_conv_halo<2, true>); break;
+            case 4: launch(k_conv_halo<4, true>); break;
+            default: launch(k_conv_halo<8, true>); break;
+        }
+    } else {
+        switch (R) {
+            case 1: launch(k_conv_halo<1, false>); break;
+            case 2: launch(k_conv_halo<2, false>); break;
+            case 4: launch(k_conv_halo<4, false>); break;
+            default: launch(k_conv_halo<8, false>); break;
+        }
+    }
     return true;
 }
 
