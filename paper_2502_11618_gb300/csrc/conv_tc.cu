@@ -1044,12 +1044,8 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.err = g_err;
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 + 4 * (size_t)N;
     const int grid = std::min(p.ntiles, g_num_sms);
-    auto launch = [&](auto kern) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr = true;
-        }
+    auto launch = [&](void (*kern)(HParams)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         kern<<<grid, kThreads, smem, st>>>(p);
     };
     if (p.parity) {
