@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdlib>
+#include <type_traits>
 #include <cstring>
 
 #include "lnr_internal.h"
@@ -417,7 +418,7 @@ struct HSeg {
 struct HParams {
     HSeg seg[2];
     int nseg;
-    int R, parity, W, H, B, N;
+    int R, parity, W, H, B, N;  // parity: parity classes per tile (0 = standard tiles)
     int tiles_x, tiles_y, ntiles;
     int stages;
     uint32_t stage_bytes, tmem_cols, idesc;
@@ -473,7 +474,11 @@ __device__ __forceinline__ uint64_t sdesc_hi(uint32_t sbo, uint32_t swz) {
     return ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swz << 61);
 }
 
-template <int R, bool PAR>
+// PAR = 0: standard tiles of R rows x 128 columns.  PAR = 1, 2 or 4: the decoder's first
+// conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
+// (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
+// class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
+template <int R, int PAR>
 __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -489,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
     float* sbias = reinterpret_cast<float*>(gbase + (tslot - base) + 16);
+    float* shw = sbias + p.N;             // head weights [head_o][N], then head bias
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
     if (threadIdx.x == 0) {
@@ -505,6 +511,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = threadIdx.x; i < N; i += kThreads) sbias[i] = p.bias[i];
+    if (p.head_out)
+        for (int i = threadIdx.x; i < p.head_o * (N + 1); i += kThreads)
+            shw[i] = i < p.head_o * N ? p.head_w[i] : p.head_b[i - p.head_o * N];
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
@@ -514,13 +523,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     // tile t -> image n, first column x0 and first row y0 (coarse for parity tiles) and the
     // parity class (px, py); parity is the fastest index so that the four classes of a
     // region run back to back and share its halo in L2
+    // (for PAR 1 and 2, px / py are the tile's class; PAR 4 covers every class)
     auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
-        if (PAR) {
+        px = py = 0;
+        if (PAR == 1) {
             px = t & 1;
             py = (t >> 1) & 1;
             t >>= 2;
-        } else {
-            px = py = 0;
+        } else if (PAR == 2) {
+            py = t & 1;
+            t >>= 1;
         }
         const int tx = t % p.tiles_x;
         t /= p.tiles_x;
@@ -546,8 +558,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     mbar_expect_tx(full(st), s.bytes);
                     const int c = cc * s.ck;
                     if (PAR && sg == 0) {
-                        tma_5d(a_dst, &s.a, full(st), c, 0, x0 - 1, 2 * y0 + py - 1, n);
-                        tma_5d(a_dst + s.plane, &s.a, full(st), c, 1, x0 - 1, 2 * y0 + py - 1, n);
+                        const int fy = PAR == 4 ? 2 * y0 - 1 : 2 * y0 + py - 1;  // first staged fine row
+                        tma_5d(a_dst, &s.a, full(st), c, 0, x0 - 1, fy, n);
+                        tma_5d(a_dst + s.plane, &s.a, full(st), c, 1, x0 - 1, fy, n);
                     } else {
                         tma_4d(a_dst, &s.a, full(st), c, x0 - 1, y0 - 1, n);
                     }
@@ -570,7 +583,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             const int b = tcount & 1;
             if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t d0 = tmem + (uint32_t)(b * R * N);
+            constexpr int NACC = R * (PAR == 0 ? 1 : PAR);
+            const uint32_t d0 = tmem + (uint32_t)(b * NACC * N);
             uint32_t first = 1;
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
@@ -578,18 +592,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                 const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
                 const int nk = s.ck >> 4;
                 const bool skip = PAR && sg == 0, coarse = PAR && sg == 1;
-                // per-tap offset (16-byte units) of output row 0, and the row step
-                uint32_t off[9];
+                constexpr int NC = PAR == 0 ? 1 : PAR;  // parity classes in the tile
+                // per class and tap: offset (16-byte units) of output row 0; row step
+                uint32_t off[NC][9];
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int ky = tap / 3, kx = tap % 3;
-                    if (skip) {
-                        const int dxf = px + kx - 1;
-                        off[tap] = (uint32_t)(dxf & 1) * (s.plane >> 4) + ky * row16 + (uint32_t)(1 + (dxf >> 1)) * pitch16;
-                    } else if (coarse) {
-                        off[tap] = (uint32_t)(1 + ((py + ky - 1) >> 1)) * row16 + (uint32_t)(1 + ((px + kx - 1) >> 1)) * pitch16;
-                    } else {
-                        off[tap] = ky * row16 + kx * pitch16;
+                for (int c = 0; c < NC; ++c) {
+                    const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
+                    const int cpy = PAR == 4 ? (c >> 1) : py;
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap % 3;
+                        if (skip) {
+                            const int dxf = cpx + kx - 1;
+                            const int row = (PAR == 4 ? cpy : 0) + ky;  // staged fine row of output row 0
+                            off[c][tap] = (uint32_t)(dxf & 1) * (s.plane >> 4) + row * row16 +
+                                          (uint32_t)(1 + (dxf >> 1)) * pitch16;
+                        } else if (coarse) {
+                            off[c][tap] = (uint32_t)(1 + ((cpy + ky - 1) >> 1)) * row16 +
+                                          (uint32_t)(1 + ((cpx + kx - 1) >> 1)) * pitch16;
+                        } else {
+                            off[c][tap] = ky * row16 + kx * pitch16;
+                        }
                     }
                 }
                 const uint32_t rstep = skip ? 2 * row16 : row16;
@@ -604,11 +627,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     for (int tap = 0; tap < 9; ++tap) {
                         for (int k = 0; k < nk; ++k) {
                             const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
-                            const uint32_t ab = a0 + off[tap] + 2 * k;
                             const uint32_t acc = first ? 0u : 1u;
 #pragma unroll
-                            for (int r = 0; r < R; ++r)
-                                mma_bf16(d0 + (uint32_t)(r * N), hi | (uint64_t)(ab + r * rstep), bd, p.idesc, acc);
+                            for (int c = 0; c < NC; ++c) {
+                                const uint32_t ab = a0 + off[c][tap] + 2 * k;
+#pragma unroll
+                                for (int r = 0; r < R; ++r)
+                                    mma_bf16(d0 + (uint32_t)((c * R + r) * N), hi | (uint64_t)(ab + r * rstep), bd, p.idesc,
+                                             acc);
+                            }
                             first = 0;
                         }
                     }
@@ -640,7 +667,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             tc_fence_after();
             int n, x0, y0, px, py;
             tile_of(t, n, x0, y0, px, py);
-            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * R * N);
+            constexpr int NCE = PAR == 0 ? 1 : PAR;
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NCE * R * N);
             if (pool) {
                 // rows in pairs: both rows stored, their 2x2 maximum pooled with the lane
                 // that holds the neighbouring column
@@ -669,12 +697,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     }
                 }
             } else {
-                for (int r = 0; r < R; ++r) {
+                for (int a = 0; a < NCE * R; ++a) {
+                    const int c = a / R, r = a % R;
                     int x, y;
                     bool v;
                     if (PAR) {
-                        x = 2 * (x0 + m) + px;
-                        y = 2 * (y0 + r) + py;
+                        const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
+                        const int cpy = PAR == 4 ? (c >> 1) : py;
+                        x = 2 * (x0 + m) + cpx;
+                        y = 2 * (y0 + r) + cpy;
                         v = (x0 + m) < Wh && (y0 + r) < Hh;
                     } else {
                         x = x0 + m;
@@ -686,8 +717,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     for (int c0 = 0; c0 < N; c0 += 32) {
                         uint32_t u0[16], u1[16];
                         const bool two = c0 + 16 < N;
-                        tmem_ld16_async(trow + (uint32_t)(r * N + c0), u0);
-                        if (two) tmem_ld16_async(trow + (uint32_t)(r * N + c0 + 16), u1);
+                        tmem_ld16_async(trow + (uint32_t)(a * N + c0), u0);
+                        if (two) tmem_ld16_async(trow + (uint32_t)(a * N + c0 + 16), u1);
                         tmem_wait16(u0);
                         if (two) tmem_wait16(u1);
                         float f0[16], f1[16];
@@ -701,8 +732,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                                 float sacc = 0.f;
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
-                                    sacc = fmaf(__ldg(p.head_w + o * N + c0 + j), f0[j], sacc);
-                                    if (two) sacc = fmaf(__ldg(p.head_w + o * N + c0 + 16 + j), f1[j], sacc);
+                                    sacc = fmaf(shw[o * N + c0 + j], f0[j], sacc);
+                                    if (two) sacc = fmaf(shw[o * N + c0 + 16 + j], f1[j], sacc);
                                 }
                                 h[o] += sacc;
                             }
@@ -713,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     }
                     if (p.head_out && v)
                         for (int o = 0; o < p.head_o; ++o)
-                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + __ldg(p.head_b + o))));
+                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[p.head_o * N + o])));
                 }
             }
             tc_fence_before();
@@ -916,55 +947,65 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
     return cudaMemcpy(dst, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
 }
 
-// Bytes of one pipeline stage of the halo kernel for a layer at tile height R and chunks
-// of at most ckmax channels (the larger of its K segments).
-static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int ckmax) {
+// Bytes of one pipeline stage of the halo kernel for a layer at tile height R, P parity
+// classes per tile (decoder concat convs) and chunks of at most ckmax channels.
+static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax) {
     const int segC[2] = {tc_c0(L), L.cin1};
     uint32_t st = 0;
     for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg) {
         const int ck = seg_ck(segC[sg], ckmax);
         const int kind1 = L.cin1 && sg == 0;
-        const uint32_t rows = kind1 ? 2 * R + 1 : R + 2, pitch = 2 * ck;
+        const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = 2 * ck;
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + 9u * L.cout * pitch, 1024));
     }
     return st;
 }
 
-// Default halo tile of a layer: the tallest tile whose R*N accumulator columns fit TMEM
-// twice (even R when the layer pools), then the widest chunk (64, then 32 channels) that
-// leaves at least two pipeline stages; 16-channel chunks only as a last resort.
-void halo_default(const ConvLayer& L, int& R, int& ckmax) {
+// Default halo tile of a layer: the most pixels per tile (P parity classes x R rows x 128
+// columns) whose P*R*N accumulator columns fit TMEM twice (even R when the layer pools),
+// then the widest chunk (64, then 32 channels) that leaves two pipeline stages; 16-channel
+// chunks only as a last resort.
+void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
     const int N = L.cout;
-    int rmax = std::min(8, 256 / N);
+    const int Ps[3] = {4, 2, 1};
     for (int pass = 0; pass < 2; ++pass)
-        for (int r = rmax; r >= 1; r = r > 1 ? r / 2 : 0) {
-            if (L.pool && (r & 1)) continue;
-            const int cks[2] = {64, 32};
-            for (int i = 0; i < (pass ? 1 : 2); ++i) {
-                const int ck = pass ? 16 : cks[i];
-                if (halo_stage_bytes(L, r, ck) * 2 <= 220u * 1024u) {
-                    R = r;
-                    ckmax = ck;
-                    return;
+        for (int area = 8; area >= 1; area /= 2)
+            for (int pi = 0; pi < (L.cin1 ? 3 : 1); ++pi) {
+                const int pp = L.cin1 ? Ps[pi] : 1;
+                if (area % pp) continue;
+                const int r = area / pp;
+                if (2 * area * N > 512 || (L.pool && (r & 1))) continue;
+                const int cks[2] = {64, 32};
+                for (int i = 0; i < (pass ? 1 : 2); ++i) {
+                    const int ck = pass ? 16 : cks[i];
+                    if (halo_stage_bytes(L, r, pp, ck) * 2 <= 220u * 1024u) {
+                        R = r;
+                        P = L.cin1 ? pp : 0;
+                        ckmax = ck;
+                        return;
+                    }
                 }
             }
-        }
     R = 1;
+    P = L.cin1 ? 1 : 0;
     ckmax = 16;
 }
 
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
-                  int ckmax, cudaStream_t st) {
+                  int P, int ckmax, cudaStream_t st) {
     const __nv_bfloat16* wh = static_cast<const __nv_bfloat16*>(L.wh[ck_index(ckmax)]);
     if (!wh) return false;
     HParams p;
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout, c0 = tc_c0(L);
-    if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * R * N > 512 || (L.pool && (R & 1))) return false;
+    if (!L.cin1) P = 0;
+    else if (P != 1 && P != 2 && P != 4) return false;
+    const int NC = P ? P : 1;
+    if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * NC * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
-    p.parity = L.cin1 > 0;
+    p.parity = P;
     const cuuint64_t eb = 2;
     size_t w_off = 0;  // elements into wh
     uint32_t stage = 0;
@@ -973,7 +1014,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.ck = seg_ck(C, ckmax);
         s.pitch = (uint32_t)s.ck * 2;
         s.swz = umma_layout_for(s.ck);
-        s.rows = kind == 1 ? 2 * R + 1 : R + 2;
+        s.rows = kind == 1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2;
         s.nchunk = C / s.ck;
         const uint32_t planes = kind == 1 ? 2 : 1;
         s.plane = align_up((uint32_t)s.rows * kHaloW * s.pitch, 1024);
@@ -1015,7 +1056,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         ok = set_seg(p.seg[1], 2, src1, L.cin1, W / 2, H / 2) && ok;
         p.tiles_x = (W / 2 + 127) / 128;
         p.tiles_y = (H / 2 + R - 1) / R;
-        p.ntiles = B * 4 * p.tiles_y * p.tiles_x;
+        p.ntiles = B * (4 / P) * p.tiles_y * p.tiles_x;
     } else {
         p.nseg = 1;
         ok = set_seg(p.seg[0], 0, src0, c0, W, H);
@@ -1031,7 +1072,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         return true;
     }
     uint32_t cols = 32;
-    while (cols < 2u * R * N) cols <<= 1;
+    while (cols < 2u * NC * R * N) cols <<= 1;
     p.tmem_cols = cols;
     p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     p.bias = L.b32;
@@ -1042,26 +1083,27 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
-    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 + 4 * (size_t)N;
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 +
+                        4 * (size_t)(N + head_o * (N + 1));
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams)) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         kern<<<grid, kThreads, smem, st>>>(p);
     };
-    if (p.parity) {
+    auto pick = [&](auto par) {
+        constexpr int PP = decltype(par)::value;
         switch (R) {
-            case 1: launch(k_conv_halo<1, true>); break;
-            case 2: launch(k_conv_halo<2, true>); break;
-            case 4: launch(k_conv_halo<4, true>); break;
-            default: launch(k_conv_halo<8, true>); break;
+            case 1: launch(k_conv_halo<1, PP>); break;
+            case 2: launch(k_conv_halo<2, PP>); break;
+            case 4: launch(k_conv_halo<4, PP>); break;
+            default: launch(k_conv_halo<8, PP>); break;
         }
-    } else {
-        switch (R) {
-            case 1: launch(k_conv_halo<1, false>); break;
-            case 2: launch(k_conv_halo<2, false>); break;
-            case 4: launch(k_conv_halo<4, false>); break;
-            default: launch(k_conv_halo<8, false>); break;
-        }
+    };
+    switch (P) {
+        case 0: pick(std::integral_constant<int, 0>{}); break;
+        case 1: pick(std::integral_constant<int, 1>{}); break;
+        case 2: pick(std::integral_constant<int, 2>{}); break;
+        default: pick(std::integral_constant<int, 4>{}); break;
     }
     return true;
 }
@@ -1073,13 +1115,14 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     tc_init();
     static const int forced = [] {
         const char* e = getenv("LNR_CONV_KERNEL");
-        return (e && !strcmp(e, "generic")) ? 2 : 0;
+        return (e && !strcmp(e, "generic")) ? 2 : (e && !strcmp(e, "halo")) ? 3 : 0;
     }();
-    const int mode = forced ? forced : L.tc_mode;
+    int mode = forced == 3 ? 0 : forced ? forced : L.tc_mode;
+    if (mode == 0 && L.cout >= 256 && forced != 3) mode = 2;  // B traffic per 128-row tile favours the generic kernel there
     if (mode != 2) {
-        int R = L.tc_R, CK = L.tc_CK;
-        if (mode == 0) halo_default(L, R, CK);
-        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, CK, st)) return;
+        int R = L.tc_R, P = L.tc_P, CK = L.tc_CK;
+        if (mode == 0) halo_default(L, R, P, CK);
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, st)) return;
     }
     tc_conv_generic(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, st);
 }

@@ -47,7 +47,7 @@ struct ConvLayer {
     void* wtc = nullptr;    // device, tensor-core weights [cout][tap][cin_pad] (bf16 or fp8)
     void* wh[3] = {nullptr, nullptr, nullptr};  // device, halo-kernel weights for chunks of <= 16 / 32 / 64 channels
     int tc_mode = 0;        // 0: halo kernel, default tile; 1: halo kernel, tc_R x tc_CK; 2: generic kernel
-    int tc_R = 0, tc_CK = 0;
+    int tc_R = 0, tc_P = 0, tc_CK = 0;
     float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null
     std::vector<float> wf;  // host FP32 OIHW after batch-norm folding
     std::vector<float> bf;
