@@ -24,6 +24,7 @@
 // Every mbarrier wait is bounded (about 2 s); a wait that runs out sets an error word and
 // the CTA drains its copies, frees its TMEM and exits.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cstdlib>
@@ -762,6 +763,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
 
 // ------------------------------------------------------------------ host side ----
 
+// cuTensorMapEncodeTiled through the runtime's driver entry-point lookup, so that the
+// library links no driver library and loads on machines without one.
+static CUresult encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, cuuint32_t rank, void* addr, const cuuint64_t* dims,
+                             const cuuint64_t* strides, const cuuint32_t* box, const cuuint32_t* es,
+                             CUtensorMapInterleave il, CUtensorMapSwizzle sw, CUtensorMapL2promotion l2,
+                             CUtensorMapFloatOOBfill oob) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    if (!fn) return CUDA_ERROR_NOT_SUPPORTED;
+    return fn(m, dt, rank, addr, dims, strides, box, es, il, sw, l2, oob);
+}
+
 // Chunk width of a K segment of C channels (C a multiple of 16): the largest of 64, 32, 16
 // that is at most ckmax and divides C.
 int seg_ck(int C, int ckmax) {
@@ -778,7 +797,7 @@ uint32_t umma_layout_for(int kc) { return kc == 64 ? 2u : kc == 32 ? 4u : 6u; }
 bool encode(CUtensorMap* m, int rank, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
             const cuuint32_t* box, int kc) {
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims,
+    CUresult r = encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims,
                                         strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(kc),
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -1029,21 +1048,21 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             cuuint64_t dims[5] = {(cuuint64_t)C, 2, (cuuint64_t)Ws / 2, (cuuint64_t)Hs, (cuuint64_t)B};
             cuuint64_t str[4] = {C * eb, 2 * C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
             cuuint32_t box[5] = {(cuuint32_t)s.ck, 1, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-            ok = cuTensorMapEncodeTiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(src), dims, str, box, es,
+            ok = encode_tiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(src), dims, str, box, es,
                                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         } else {
             cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
             cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
             cuuint32_t box[4] = {(cuuint32_t)s.ck, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-            ok = cuTensorMapEncodeTiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(src), dims, str, box, es,
+            ok = encode_tiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(src), dims, str, box, es,
                                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
         cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)9 * s.nchunk};
         cuuint64_t wstr[2] = {s.ck * eb, (cuuint64_t)N * s.ck * eb};
         cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, 9};
-        ok = ok && cuTensorMapEncodeTiled(&s.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(wh + w_off),
+        ok = ok && encode_tiled(&s.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(wh + w_off),
                                           wd, wstr, wbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck),
                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         w_off += (size_t)s.nchunk * 9 * N * s.ck;
