@@ -168,6 +168,26 @@ lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[4]);
 lnr_status lnr_set_timing(lnr_ctx* ctx, int enable);
 lnr_status lnr_get_timing(lnr_ctx* ctx, double out[8]);
 
+/* ---- filter without allocation ------------------------------------------------------ */
+
+/* The depth-guided filter alone (Fig. 2), for callers that may not allocate device memory
+ * -- e.g. a host application's real-time frame loop, where cudaMalloc can synchronise the
+ * whole device and stall unrelated work, or a plug-in whose host owns every allocation.
+ * The paper has no counterpart: it is a deployment variant of the filter stage of
+ * lnr_render, with the same arithmetic (kept depth bit-identical to LNR_STAGE_FILTERED).
+ * d_depth: device float [H*W], view-space depth, +inf where no point was projected.
+ * d_kept:  device float [H*W] output, the kept depth, +inf where empty or filtered out.
+ * n_levels, fs: as lnr_render.  cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * Runs on the current CUDA device and allocates nothing: the pyramid lives in a fixed
+ * 12 MiB device array inside the library (held by every GPU that loads it until exit),
+ * enough for images up to about 2560 x 1440 at 6 levels; larger images return LNR_E_ARG.
+ * The first call on a device looks up that array's address; make it before any stream
+ * capture.  Calls whose work overlaps on the GPU share the array and race; order them.
+ * Returns without waiting for the GPU.  Errors: LNR_E_ARG (null pointer, bad size, level
+ * count or strength), LNR_E_CUDA (a launch failed). */
+lnr_status lnr_filter_static(const float* d_depth, int W, int H, int n_levels, float fs, float* d_kept,
+                             void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

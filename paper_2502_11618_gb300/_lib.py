@@ -24,7 +24,8 @@ E_BUSY = -6
 SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr_build_grid",
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
-           "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing"]
+           "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
+           "lnr_filter_static"]
 
 
 class LnrError(RuntimeError):
@@ -80,6 +81,7 @@ def lib():
             "lnr_serve_stats": ([p, p], st),
             "lnr_set_timing": ([p, i], st),
             "lnr_get_timing": ([p, p], st),
+            "lnr_filter_static": ([p, i, i, i, f, p, p], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

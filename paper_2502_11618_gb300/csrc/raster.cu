@@ -590,3 +590,132 @@ void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t 
 }
 
 }  // namespace lnr
+
+// ============================================ depth filter into a static scratch array ==
+//
+// lnr_filter_static runs the depth-guided filter on a caller's device depth image without
+// allocating any memory: its pyramid lives in the file-scope array below, which every GPU
+// that loads the library holds until the process exits.  Every call overwrites the whole
+// part of the array it uses, so nothing has to be cleared between calls; two calls whose
+// work overlaps on the GPU (different streams, no ordering between them) share the array
+// and race.
+
+namespace lnr {
+namespace {
+
+// 3 Mi floats (12 MiB): one view parameter block, the min-pooled levels M1..Mn and the
+// upsampled levels U1..U(n-1).  A 2560 x 1440 image with 6 levels needs about 2.5 Mi.
+constexpr size_t kStaticFilterFloats = size_t(3) << 20;
+constexpr size_t kStaticViewFloats = 64;  // ViewDev block at the front (256-byte aligned)
+static_assert(sizeof(ViewDev) <= kStaticViewFloats * sizeof(float), "view block");
+
+__device__ __align__(256) float g_filter_scratch[kStaticFilterFloats];
+
+__global__ void k_static_view(ViewDev* v, float S, float zfar) {
+    ViewDev d{};
+    d.S = S;
+    d.zfar = zfar;
+    *v = d;
+}
+
+// Min-pool pyramid of a depth image, one 64 x 64 tile per block (the same levels as the
+// resolve kernel computes from z-buffer keys).
+__global__ void __launch_bounds__(256) k_pyramid_from_depth(const float* __restrict__ depth, int W, int H, int nlev,
+                                                            float* __restrict__ pyr) {
+    __shared__ float s[64][65];
+    __shared__ float t[32][33];
+    const int x = threadIdx.x & 63, y0 = threadIdx.x >> 6;
+    const int gx = blockIdx.x * 64 + x;
+    for (int i = 0; i < 16; ++i) {
+        const int y = y0 + 4 * i, gy = blockIdx.y * 64 + y;
+        s[y][x] = (gx < W && gy < H) ? depth[(size_t)gy * W + gx] : INFINITY;
+    }
+    __syncthreads();
+    float* lev = pyr;
+    int Wl = W, Hl = H;
+    for (int l = 1; l <= nlev; ++l) {
+        const int T = 64 >> l;
+        Wl = (Wl + 1) >> 1;
+        Hl = (Hl + 1) >> 1;
+        for (int idx = threadIdx.x; idx < T * T; idx += 256) {
+            const int lx = idx % T, ly = idx / T;
+            float m;
+            if (l & 1) {
+                m = fminf(fminf(s[2 * ly][2 * lx], s[2 * ly][2 * lx + 1]), fminf(s[2 * ly + 1][2 * lx], s[2 * ly + 1][2 * lx + 1]));
+                t[ly][lx] = m;
+            } else {
+                m = fminf(fminf(t[2 * ly][2 * lx], t[2 * ly][2 * lx + 1]), fminf(t[2 * ly + 1][2 * lx], t[2 * ly + 1][2 * lx + 1]));
+                s[ly][lx] = m;
+            }
+            const int ox_ = blockIdx.x * T + lx, oy_ = blockIdx.y * T + ly;
+            if (ox_ < Wl && oy_ < Hl) lev[(size_t)oy_ * Wl + ox_] = m;
+        }
+        lev += (size_t)Wl * Hl;
+        __syncthreads();
+    }
+}
+
+float* g_static_ptr[64] = {nullptr};
+std::mutex g_static_mu;
+
+}  // namespace
+}  // namespace lnr
+
+extern "C" lnr_status lnr_filter_static(const float* d_depth, int W, int H, int n_levels, float fs, float* d_kept,
+                                        void* cuda_stream) {
+    using namespace lnr;
+    if (!d_depth || !d_kept || W < 1 || H < 1 || (int64_t)W * H > (1ll << 30)) return LNR_E_ARG;
+    int maxl = 0;
+    while ((2 << maxl) <= std::min(W, H)) ++maxl;
+    if (n_levels < 0 || n_levels > std::min(maxl, kMaxLevels) || !(fs >= 0.0f)) return LNR_E_ARG;
+    const size_t lev = pyramid_floats(W, H, n_levels);
+    if (kStaticViewFloats + 2 * lev > kStaticFilterFloats) return LNR_E_ARG;  // beyond the static capacity
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LNR_E_CUDA;
+    float* scratch;
+    {
+        std::lock_guard<std::mutex> g(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_filter_scratch) != cudaSuccess || !ptr) return LNR_E_CUDA;
+            g_static_ptr[dev] = static_cast<float*>(ptr);
+        }
+        scratch = g_static_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    ViewDev* view = reinterpret_cast<ViewDev*>(scratch);
+    float* M = scratch + kStaticViewFloats;
+    float* U = M + lev;
+    const float S = 1.0f + fs * 0.05f;  // keep scale, as for lnr_render
+    k_static_view<<<1, 1, 0, st>>>(view, S, 1.0f);
+    UpArgs a{};
+    a.views = view;
+    a.kind = 2;
+    if (n_levels == 0) {
+        a.Mf = d_depth;
+        a.f_stride = (size_t)W * H;
+        a.Wf = W;
+        a.Hf = H;
+        a.u0 = d_kept;
+        k_pack_direct<<<2048, 256, 0, st>>>(a, 1);
+        return cudaGetLastError() == cudaSuccess ? LNR_OK : LNR_E_CUDA;
+    }
+    dim3 g((W + 63) / 64, (H + 63) / 64, 1);
+    k_pyramid_from_depth<<<g, 256, 0, st>>>(d_depth, W, H, n_levels, M);
+    for (int l = n_levels - 1; l >= 0; --l) {
+        int Wl = W, Hl = H;
+        for (int k = 0; k < l; ++k) { Wl = (Wl + 1) / 2; Hl = (Hl + 1) / 2; }
+        UpArgs u = a;
+        u.Wf = Wl; u.Hf = Hl;
+        u.Wc = (Wl + 1) / 2; u.Hc = (Hl + 1) / 2;
+        u.Mf = l == 0 ? d_depth : M + pyramid_offset(W, H, l);
+        u.Mc = M + pyramid_offset(W, H, l + 1);
+        u.Uc = (l + 1 == n_levels) ? u.Mc : U + pyramid_offset(W, H, l + 1);
+        u.f_stride = u.c_stride = u.uc_stride = u.uf_stride = 0;
+        if (l > 0) { u.Uf = U + pyramid_offset(W, H, l); u.fill = 1; }
+        else { u.Uf = nullptr; u.u0 = d_kept; u.fill = 0; }
+        dim3 gu((u.Wc + 31) / 32, (u.Hc + 7) / 8, 1);
+        k_upsample<<<gu, 256, 0, st>>>(u);
+    }
+    return cudaGetLastError() == cudaSuccess ? LNR_OK : LNR_E_CUDA;
+}
