@@ -36,7 +36,9 @@ void Workspace::release() {
     pinned_view.bytes = 0;
     for (auto& e : ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
-    if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    graph_warm.clear();
 }
 
 // FP64 composition of the view with the grid (once per view, on the host): the anchor
@@ -71,7 +73,7 @@ static bool finite_view(const lnr_view& v) {
     return true;
 }
 
-static lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in,
+lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in,
                                    int W, int H, int nlev, const float* fs, bool need_unet) {
     if (!c->grid_ok) return fail(c, LNR_E_STATE, "render before build_grid");
     if (need_unet && !c->unet_ok) return fail(c, LNR_E_STATE, "render before set_unet");
@@ -99,6 +101,8 @@ static lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views
 // Size every per-frame buffer for B views of W x H with nlev pyramid levels.
 static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int H, int nlev) {
     cudaError_t e;
+    const void* before[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
+                            ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p};
     const size_t P = (size_t)W * H;
     const int nb = cull_blocks(c->ncells);
     const size_t pf = pyramid_floats(W, H, kMaxLevels);
@@ -120,6 +124,10 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
     if (!ws.ev[0])
         for (auto& ev : ws.ev)
             if ((e = cudaEventCreate(&ev))) return e;
+    const void* after[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
+                           ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p};
+    for (size_t i = 0; i < sizeof(before) / sizeof(before[0]); ++i)
+        if (before[i] != after[i]) ws.alloc_gen++;
     ws.B = B;
     ws.W = W;
     ws.H = H;
@@ -129,7 +137,7 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
 
 // Enqueue one batch on `st`: params upload, cull, splat, resolve + pyramid, upsampling,
 // U-Net.  stage < 0 runs the whole frame into ws.out; otherwise stops after that stage.
-static void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec,
+void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec,
                           bool timed) {
     cudaEvent_t* ev = ws.ev;
     auto mark = [&](int i) {
@@ -160,18 +168,74 @@ static void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage,
     mark(5);
 }
 
-static lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in,
+lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in,
                                 int W, int H, int nlev, const float* fs) {
     cudaError_t e = ensure_ws(c, ws, B, W, H, nlev);
     if (e != cudaSuccess) return cuda_fail(c, e, "workspace");
+    const void* in_before = ws.act[4 * kMaxUnetLevels].p;
     e = ws.act[4 * kMaxUnetLevels].ensure((size_t)B * W * H * 8 * 4 + 256);
     if (e != cudaSuccess) return cuda_fail(c, e, "U-Net input");
+    if (in_before != ws.act[4 * kMaxUnetLevels].p) ws.alloc_gen++;
+    if (c->unet_ok) {
+        e = unet_ensure(c->unet, ws, c->prec == LNR_FP32 ? LNR_FP32 : LNR_BF16);
+        if (e == cudaSuccess && c->prec != LNR_FP32) e = unet_ensure(c->unet, ws, LNR_FP32);
+        if (e != cudaSuccess) return cuda_fail(c, e, "U-Net activations");
+    }
     ViewDev* hv = ws.pinned_view.as<ViewDev>();
     // the pinned block may still feed an earlier launch on this stream
     e = cudaStreamSynchronize(ws.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream");
     for (int i = 0; i < B; ++i) compose_view(c, views[i], in[i], fs[i], hv[i]);
     return LNR_OK;
+}
+
+size_t frame_bytes(int B, int W, int H) {
+    const size_t P = (size_t)B * W * H;
+    // keys 8, depth 4, rgba 4, kept depth 4, output 12, U-Net input 32 bytes per pixel, pyramid
+    return P * 64 + 8 * (size_t)B * pyramid_floats(W, H, kMaxLevels);
+}
+
+// Enqueue a whole frame batch on ws.stream: replayed from a CUDA graph captured for this
+// (batch, size, levels, precision) once the configuration has run eagerly once; graphs are
+// dropped whenever a buffer they captured was reallocated or the cloud / net changed.
+cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph) {
+    if (!use_graph) {
+        enqueue_frame(c, ws, ws.stream, -1, prec, false);
+        return cudaGetLastError();
+    }
+    const GraphKey key{ws.B, ws.W, ws.H, ws.nlev, (int)prec};
+    if (ws.graph_gen != ws.alloc_gen || ws.graph_cloud != c->cloud_gen || ws.graph_unet != c->unet_gen) {
+        for (auto& kv : ws.graphs) cudaGraphExecDestroy(kv.second);
+        ws.graphs.clear();
+        ws.graph_warm.clear();
+        ws.graph_gen = ws.alloc_gen;
+        ws.graph_cloud = c->cloud_gen;
+        ws.graph_unet = c->unet_gen;
+    }
+    auto it = ws.graphs.find(key);
+    if (it == ws.graphs.end()) {
+        if (!ws.graph_warm.count(key) || ws.keys_dirty) {  // first run of this configuration: eager
+            ws.graph_warm.insert(key);
+            enqueue_frame(c, ws, ws.stream, -1, prec, false);
+            return cudaGetLastError();
+        }
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ws.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_frame(c, ws, ws.stream, -1, prec, false);
+            e = cudaStreamEndCapture(ws.stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {  // capture not possible on this stream: stay eager
+            cudaGetLastError();
+            enqueue_frame(c, ws, ws.stream, -1, prec, false);
+            return cudaGetLastError();
+        }
+        it = ws.graphs.emplace(key, ex).first;
+    }
+    return cudaGraphLaunch(it->second, ws.stream);
 }
 
 static void read_timing(lnr_ctx* c, Workspace& ws) {
@@ -431,7 +495,11 @@ lnr_status lnr_render_batch(lnr_ctx* c, int nviews, const lnr_view* views, const
     Workspace& ws = c->ws;
     s = prepare_views(c, ws, nviews, views, in, W, H, nlev, fs);
     if (s != LNR_OK) return s;
-    enqueue_frame(c, ws, ws.stream, -1, c->prec, c->timing);
+    if (c->timing) enqueue_frame(c, ws, ws.stream, -1, c->prec, true);
+    else {
+        cudaError_t e = run_frame(c, ws, c->prec, true);
+        if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
+    }
     return finish_output(c, ws, out, (size_t)nviews * W * H * 3, on_device);
 }
 

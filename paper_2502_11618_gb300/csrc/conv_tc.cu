@@ -1106,7 +1106,13 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                         4 * (size_t)(N + head_o * (N + 1));
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams)) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        static std::mutex mu;
+        static std::set<const void*> done;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (done.insert((const void*)kern).second)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        }
         kern<<<grid, kThreads, smem, st>>>(p);
     };
     auto pick = [&](auto par) {

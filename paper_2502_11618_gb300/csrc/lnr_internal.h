@@ -8,6 +8,8 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <set>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -85,6 +87,13 @@ struct DBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+struct GraphKey {
+    int B, W, H, nlev, prec;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(B, W, H, nlev, prec) < std::tie(o.B, o.W, o.H, o.nlev, o.prec);
+    }
+};
+
 // Per-launch workspace: everything one batch of views needs on the device.
 struct Workspace {
     int B = 0, W = 0, H = 0, nlev = 0;
@@ -101,11 +110,11 @@ struct Workspace {
     DBuf pinned_view;                       // host pinned ViewDev[B]
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[16] = {nullptr};
-    // CUDA graph of the whole frame for (B, W, H, nlev, precision)
-    cudaGraphExec_t graph = nullptr;
-    int g_B = -1, g_W = -1, g_H = -1, g_nlev = -1, g_prec = -1;
-    uint64_t g_cloud_gen = 0, g_unet_gen = 0;
-    std::vector<std::string> stage_names;
+    // CUDA graphs of whole frames, per (B, W, H, nlev, precision); valid while no buffer
+    // they captured has been reallocated (alloc_gen) and the cloud / net are unchanged
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::set<GraphKey> graph_warm;
+    uint64_t alloc_gen = 0, graph_gen = 0, graph_cloud = 0, graph_unet = 0;
     void release();
 };
 
@@ -181,7 +190,17 @@ size_t pyramid_floats(int W, int H, int nlev);
 size_t pyramid_offset(int W, int H, int l);
 void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t npx, cudaStream_t st);
 
+// api.cu
+lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in, int W, int H,
+                            int nlev, const float* fs, bool need_unet);
+lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in, int W,
+                         int H, int nlev, const float* fs);
+void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec, bool timed);
+cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph);
+size_t frame_bytes(int B, int W, int H);  // raster workspace bytes of a batch
+
 // unet.cu
+cudaError_t unet_ensure(const Unet& u, Workspace& ws, lnr_precision p);
 size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p);
 lnr_status unet_prepare(lnr_ctx* c);
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,

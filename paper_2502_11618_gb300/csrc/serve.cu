@@ -1,28 +1,334 @@
-// Serving loop: placeholder entry points until the continuous-batching scheduler lands.
+// Serving loop: continuous batching of render requests on one GPU.
+//
+// Requests (pose, resolution, n_levels, filter_strength) are queued by lnr_submit from any
+// thread.  A scheduler thread owns `slots` workspaces, each with its own CUDA stream and
+// buffers.  Whenever a slot is free it takes the oldest queued request and up to
+// max_batch - 1 more of the same resolution and pyramid depth, admits them if their
+// activation memory fits the budget next to the requests already on the GPU, and launches
+// the batch (a replayed CUDA graph once the configuration has been seen) followed by the
+// device-to-host copy of every result into its own pinned buffer and an event.  Work of
+// different slots overlaps on the device.  Completed requests are picked up by lnr_poll.
+// Every wait is bounded: the scheduler polls events, and lnr_serve_stop gives the device a
+// deadline before reporting a timeout.
+#include <chrono>
+#include <cstring>
+
 #include "lnr_internal.h"
 
 namespace lnr {
-struct Server {};
+
+struct Slot {
+    Workspace ws;
+    cudaEvent_t done = nullptr;
+    std::vector<uint64_t> tickets;
+    size_t act_bytes = 0;
+    bool busy = false;
+};
+
+struct PinnedPool {
+    std::multimap<size_t, float*> free_;
+    float* get(size_t bytes) {
+        auto it = free_.lower_bound(bytes);
+        if (it != free_.end() && it->first < 2 * bytes) {
+            float* p = it->second;
+            free_.erase(it);
+            return p;
+        }
+        void* p = nullptr;
+        if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+        return static_cast<float*>(p);
+    }
+    void put(float* p, size_t bytes) { free_.emplace(bytes, p); }
+    void release() {
+        for (auto& kv : free_) cudaFreeHost(kv.second);
+        free_.clear();
+    }
+};
+
+struct ServeReq {
+    lnr_view view;
+    lnr_intrinsics intr;
+    int W, H, nlev;
+    float fs;
+    double t_submit = 0, t_done = 0;
+    bool done = false, failed = false;
+    float* host = nullptr;  // pinned result, H*W*3 floats
+    size_t bytes = 0;
+};
+
+struct Server {
+    lnr_ctx* c = nullptr;
+    int max_batch = 1;
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, ServeReq> reqs;
+    std::thread th;
+    std::atomic<bool> stop{false};
+    uint64_t next_ticket = 1;
+    size_t inflight = 0;
+    PinnedPool pool;
+    lnr_precision prec = LNR_FP32;
+    // stats
+    uint64_t n_done = 0, n_launch = 0, max_b = 0, peak_bytes = 0;
+    std::string err;
+
+    void loop();
+    bool launch(Slot& s, std::vector<uint64_t>& batch);
+};
+
+static size_t request_bytes(const lnr_ctx* c, int B, int W, int H, lnr_precision p) {
+    return unet_act_bytes(c->unet, B, W, H, p) + frame_bytes(B, W, H);
+}
+
+bool Server::launch(Slot& s, std::vector<uint64_t>& batch) {
+    const int B = (int)batch.size();
+    std::vector<lnr_view> views(B);
+    std::vector<lnr_intrinsics> intr(B);
+    std::vector<float> fs(B);
+    int W, H, nlev;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (int i = 0; i < B; ++i) {
+            const ServeReq& r = reqs[batch[i]];
+            views[i] = r.view;
+            intr[i] = r.intr;
+            fs[i] = r.fs;
+        }
+        const ServeReq& r0 = reqs[batch[0]];
+        W = r0.W;
+        H = r0.H;
+        nlev = r0.nlev;
+    }
+    if (prepare_views(c, s.ws, B, views.data(), intr.data(), W, H, nlev, fs.data()) != LNR_OK) return false;
+    if (run_frame(c, s.ws, prec, true) != cudaSuccess) return false;
+    const size_t per = (size_t)W * H * 3;
+    for (int i = 0; i < B; ++i) {
+        float* dst;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            ServeReq& r = reqs[batch[i]];
+            if (!r.host) {
+                r.bytes = per * 4;
+                r.host = pool.get(r.bytes);
+            }
+            dst = r.host;
+        }
+        if (!dst || cudaMemcpyAsync(dst, s.ws.out.as<float>() + i * per, per * 4, cudaMemcpyDeviceToHost, s.ws.stream))
+            return false;
+    }
+    if (cudaEventRecord(s.done, s.ws.stream) != cudaSuccess) return false;
+    s.tickets = batch;
+    s.busy = true;
+    return true;
+}
+
+void Server::loop() {
+    cudaSetDevice(c->device);
+    while (!stop.load()) {
+        bool progressed = false;
+        // completions
+        for (auto& sp : slots) {
+            Slot& s = *sp;
+            if (!s.busy) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            const double t = now_s();
+            std::lock_guard<std::mutex> g(mu);
+            for (uint64_t tk : s.tickets) {
+                auto it = reqs.find(tk);
+                if (it == reqs.end()) continue;
+                it->second.done = true;
+                it->second.failed = q != cudaSuccess;
+                it->second.t_done = t;
+                ++n_done;
+            }
+            if (q != cudaSuccess) err = cudaGetErrorString(q);
+            inflight -= s.act_bytes;
+            s.busy = false;
+            s.tickets.clear();
+            progressed = true;
+        }
+        // admission: the oldest request plus up to max_batch-1 more of its configuration
+        for (auto& sp : slots) {
+            Slot& s = *sp;
+            if (s.busy) continue;
+            std::vector<uint64_t> batch;
+            size_t bytes = 0;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                if (queue.empty()) break;
+                const ServeReq& h = reqs[queue.front()];
+                std::vector<size_t> take;
+                for (size_t i = 0; i < queue.size() && (int)take.size() < max_batch; ++i) {
+                    const ServeReq& r = reqs[queue[i]];
+                    if (r.W == h.W && r.H == h.H && r.nlev == h.nlev) take.push_back(i);
+                }
+                bytes = request_bytes(c, (int)take.size(), h.W, h.H, prec);
+                if (c->mem_budget && inflight > 0 && inflight + bytes > c->mem_budget) {
+                    // shrink the batch until it fits next to what is in flight
+                    while (take.size() > 1 && inflight + request_bytes(c, (int)take.size(), h.W, h.H, prec) > c->mem_budget)
+                        take.pop_back();
+                    bytes = request_bytes(c, (int)take.size(), h.W, h.H, prec);
+                    if (inflight + bytes > c->mem_budget) break;  // wait for completions
+                }
+                for (size_t k = take.size(); k-- > 0;) {
+                    batch.insert(batch.begin(), queue[take[k]]);
+                    queue.erase(queue.begin() + (long)take[k]);
+                }
+                inflight += bytes;
+                peak_bytes = std::max<uint64_t>(peak_bytes, inflight);
+            }
+            s.act_bytes = bytes;
+            if (!launch(s, batch)) {
+                std::lock_guard<std::mutex> g(mu);
+                for (uint64_t tk : batch) {
+                    reqs[tk].done = true;
+                    reqs[tk].failed = true;
+                }
+                err = c->err.empty() ? "launch failed" : c->err;
+                inflight -= bytes;
+                s.busy = false;
+            } else {
+                ++n_launch;
+                max_b = std::max<uint64_t>(max_b, batch.size());
+            }
+            progressed = true;
+        }
+        if (!progressed) {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
 }  // namespace lnr
 
 using namespace lnr;
 
 extern "C" {
 
-lnr_status lnr_serve_start(lnr_ctx* c, int, int) { return c ? fail(c, LNR_E_STATE, "serving not built") : LNR_E_ARG; }
-lnr_status lnr_serve_stop(lnr_ctx* c) { return c ? LNR_OK : LNR_E_ARG; }
+lnr_status lnr_serve_start(lnr_ctx* c, int max_batch, int nslots) {
+    if (!c) return LNR_E_ARG;
+    if (c->server) return fail(c, LNR_E_STATE, "serving already started");
+    if (!c->grid_ok || !c->unet_ok) return fail(c, LNR_E_STATE, "serving needs build_grid and set_unet");
+    if (max_batch < 1 || max_batch > 64 || nslots < 1 || nslots > 16) return fail(c, LNR_E_ARG, "bad batch or slot count");
+    cudaSetDevice(c->device);
+    Server* s = new Server();
+    s->c = c;
+    s->max_batch = max_batch;
+    s->prec = c->prec;
+    for (int i = 0; i < nslots; ++i) {
+        auto sl = std::make_unique<Slot>();
+        if (cudaStreamCreateWithFlags(&sl->ws.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess) {
+            delete s;
+            return fail(c, LNR_E_CUDA, "serving streams");
+        }
+        s->slots.push_back(std::move(sl));
+    }
+    c->server = s;
+    s->th = std::thread([s] { s->loop(); });
+    return LNR_OK;
+}
+
+lnr_status lnr_serve_stop(lnr_ctx* c) {
+    if (!c) return LNR_E_ARG;
+    Server* s = c->server;
+    if (!s) return LNR_OK;
+    s->stop = true;
+    s->cv.notify_all();
+    if (s->th.joinable()) s->th.join();
+    lnr_status st = LNR_OK;
+    cudaSetDevice(c->device);
+    const double deadline = now_s() + 10.0;
+    for (auto& sl : s->slots) {
+        while (cudaStreamQuery(sl->ws.stream) == cudaErrorNotReady) {
+            if (now_s() > deadline) {
+                st = fail(c, LNR_E_TIMEOUT, "serving stop: device work did not finish in 10 s");
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        sl->ws.release();
+        cudaStreamDestroy(sl->ws.stream);
+        cudaEventDestroy(sl->done);
+    }
+    for (auto& kv : s->reqs)
+        if (kv.second.host) cudaFreeHost(kv.second.host);
+    s->pool.release();
+    c->server = nullptr;
+    delete s;
+    return st;
+}
+
 lnr_status lnr_set_memory_budget(lnr_ctx* c, size_t bytes) {
     if (!c) return LNR_E_ARG;
     c->mem_budget = bytes;
     return LNR_OK;
 }
-lnr_status lnr_submit(lnr_ctx* c, const lnr_view*, const lnr_intrinsics*, int, int, int, float, uint64_t*) {
-    return c ? fail(c, LNR_E_STATE, "serving not started") : LNR_E_ARG;
+
+lnr_status lnr_submit(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* intr, int W, int H, int nlev, float fs,
+                      uint64_t* ticket) {
+    if (!c || !ticket) return LNR_E_ARG;
+    Server* s = c->server;
+    if (!s) return fail(c, LNR_E_STATE, "serving not started");
+    std::lock_guard<std::mutex> g(s->mu);
+    lnr_status st = check_frame_args(c, 1, view, intr, W, H, nlev, &fs, true);
+    if (st != LNR_OK) return st;
+    ServeReq r;
+    r.view = *view;
+    r.intr = *intr;
+    r.W = W;
+    r.H = H;
+    r.nlev = nlev;
+    r.fs = fs;
+    r.t_submit = now_s();
+    const uint64_t t = s->next_ticket++;
+    s->reqs.emplace(t, r);
+    s->queue.push_back(t);
+    *ticket = t;
+    s->cv.notify_one();
+    return LNR_OK;
 }
-lnr_status lnr_poll(lnr_ctx* c, uint64_t, float*, double*) { return c ? fail(c, LNR_E_STATE, "serving not started") : LNR_E_ARG; }
+
+lnr_status lnr_poll(lnr_ctx* c, uint64_t ticket, float* out, double* latency_s) {
+    if (!c) return LNR_E_ARG;
+    Server* s = c->server;
+    if (!s) return fail(c, LNR_E_STATE, "serving not started");
+    ServeReq r;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return fail(c, LNR_E_ARG, "unknown ticket");
+        if (!it->second.done) return LNR_E_BUSY;
+        r = it->second;
+        s->reqs.erase(it);
+    }
+    lnr_status st = LNR_OK;
+    if (r.failed) st = fail(c, LNR_E_CUDA, "request failed: " + s->err);
+    else if (out && r.host) std::memcpy(out, r.host, r.bytes);
+    if (latency_s) *latency_s = r.t_done - r.t_submit;
+    if (r.host) {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->pool.put(r.host, r.bytes);
+    }
+    return st;
+}
+
 lnr_status lnr_serve_stats(lnr_ctx* c, uint64_t out[4]) {
     if (!c || !out) return LNR_E_ARG;
-    for (int i = 0; i < 4; ++i) out[i] = 0;
+    Server* s = c->server;
+    if (!s) {
+        for (int i = 0; i < 4; ++i) out[i] = 0;
+        return LNR_OK;
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    out[0] = s->n_done;
+    out[1] = s->n_launch;
+    out[2] = s->max_b;
+    out[3] = s->peak_bytes;
     return LNR_OK;
 }
 

@@ -177,15 +177,18 @@ size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p) {
     return tot;
 }
 
-// Ensure the activation buffers of the workspace for (B, W, H).
-static cudaError_t ensure_acts(const Unet& u, Workspace& ws, lnr_precision p) {
+// Ensure the activation buffers of the workspace for (B, W, H); a reallocation bumps the
+// workspace's allocation generation (captured graphs must be rebuilt).
+cudaError_t unet_ensure(const Unet& u, Workspace& ws, lnr_precision p) {
     const size_t e = elem_bytes(p);
     cudaError_t err;
     for (int l = 0; l < u.levels; ++l) {
         size_t Pl = (size_t)ws.B * (ws.W >> l) * (ws.H >> l);
         for (int k = 0; k < 4; ++k) {
             size_t n = (k == 2) ? (size_t)ws.B * (ws.W >> (l + 1)) * (ws.H >> (l + 1)) * u.ch[l] : Pl * u.ch[l];
+            const void* before = ws.act[slot(l, k)].p;
             if ((err = ws.act[slot(l, k)].ensure(n * e + 256))) return err;
+            if (before != ws.act[slot(l, k)].p) ws.alloc_gen++;
         }
     }
     return cudaSuccess;
@@ -194,7 +197,7 @@ static cudaError_t ensure_acts(const Unet& u, Workspace& ws, lnr_precision p) {
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
                   cudaStream_t st, cudaEvent_t* layer_ev) {
     const Unet& u = c->unet;
-    if (ensure_acts(u, ws, p) != cudaSuccess) return;
+    if (unet_ensure(u, ws, p) != cudaSuccess) return;
     const int L = u.levels;
     int ci = 0;
     const void* x = in;
