@@ -121,12 +121,17 @@ def make_workload(device):
     return scene, views, weights
 
 
-def cpu_sample(scene, views, weights, crop=(480, 272)):
+def oracle_grid(scene):
+    import oracle
+    return oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
+
+
+def cpu_sample(g, views, weights, crop=(480, 272)):
     """Oracle time of one 1080p frame: cull + splat + filter of a full view (one thread),
-    the FP64 U-Net on a crop scaled by pixel count to the full frame (all cores)."""
+    the FP64 U-Net on a crop scaled by pixel count to the full frame (all cores).  The
+    grid `g` is built once per cloud, outside the sample."""
     import oracle
     import synth
-    g = oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
     intr = synth.intrinsics_for(W, H)
     t0 = time.perf_counter()
     ref = oracle.render(g, views[0], intr, W, H, NLEV, FS[0])
@@ -149,9 +154,10 @@ def run_reference(args):
     if rank != 0:
         return
     scene, views, weights = make_workload("cpu")
+    g = oracle_grid(scene)
     times = []
     for i in range(args.warmup + args.steps):
-        r = cpu_sample(scene, [views[i % len(views)]], weights)
+        r = cpu_sample(g, [views[i % len(views)]], weights)
         if i >= args.warmup:
             times.append(1.0 / r["value"])
     v = len(times) / sum(times)
@@ -244,7 +250,6 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     step_ms, wall = timed(step, args.steps, args.warmup)
-    clk = clocks.stop()
     tot_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([tot_ms], device=dev)
@@ -262,22 +267,23 @@ def main():
         tims.append(r.get_timing())
     r.set_timing(False)
     unet_ms = float(np.median([t["unet"] for t in tims]))
-    splat_ms = float(np.median([t["splat"] for t in tims]))
     pk = peaks()
     flops = unet_flops_per_px(CH) * W * H * B
     if have_tc:
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof = {"kernel": "conv3x3 tcgen05 (all U-Net conv launches)", "bound": "tensor",
-                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+        roof = {"kernel": "conv3x3 tcgen05 (all U-Net conv launches of a step)", "bound": "tensor",
+                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "measured (bf16_tflops_sustained)"}
     else:
-        smax = (clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0))
+        smax = pk.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * smax * 1e6 / 1e12
-        roof = {"kernel": "conv3x3 FP32 SIMT (all U-Net conv launches)", "bound": "alu",
-                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+        roof = {"kernel": "conv3x3 FP32 SIMT (all U-Net conv launches of a step)", "bound": "alu",
+                "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
 
-    # ---- plain per-frame FP32 path -------------------------------------------------
+    # ---- plain per-frame FP32 path (device-timed) ----------------------------------
     r.set_precision("fp32")
     out1 = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
 
@@ -287,25 +293,61 @@ def main():
     plain_ms, _ = timed(step_plain, max(3, args.steps // 2), 3)
     plain_fps = 1e3 / float(np.mean(plain_ms))
 
-    # ---- end to end through the public API, host buffers ---------------------------
+    # ---- served paths through the public serving API (host result buffers) --------
+    def serve_run(precision, max_batch, slots, n, lam, seed):
+        """Submit n 1080p requests (all at once when lam is None, else Poisson arrivals at
+        rate lam); poll every result into a host buffer; return frames/s and latencies."""
+        r.set_precision(precision)
+        r.serve_start(max_batch=max_batch, slots=slots)
+        rng = np.random.default_rng(seed)
+        img = np.empty((H, W, 3), np.float32)
+        lat, pending = [], []
+        try:
+            # warm the configuration (graph capture, pinned buffers)
+            for k in range(2 * max_batch * slots):
+                pending.append(r.submit(pose(k), intr, W, H, NLEV, FS[k % 2]))
+            for tk in pending:
+                while r.poll(tk, img)[0] is None:
+                    pass
+            pending = []
+            arrivals = np.zeros(n) if lam is None else np.cumsum(rng.exponential(1.0 / lam, size=n))
+            t0 = time.perf_counter()
+            i = 0
+            while i < n or pending:
+                now = time.perf_counter() - t0
+                while i < n and arrivals[i] <= now:
+                    pending.append(r.submit(pose(1000 + i), intr, W, H, NLEV, FS[i % 2]))
+                    i += 1
+                still = []
+                for tk in pending:
+                    res, l = r.poll(tk, img)
+                    if res is None:
+                        still.append(tk)
+                    else:
+                        lat.append(l)
+                pending = still
+            span = time.perf_counter() - t0
+        finally:
+            r.serve_stop()
+        return n / span, 1e3 * np.asarray(lat)
+
+    lam = 0.7 * plain_fps                      # both paths stable at this arrival rate
+    n_open = max(40, int(3 * lam))             # about 3 s of arrivals
+    prec_fast = "bf16" if have_tc else "fp32"
+    srv_fps, srv_closed_lat = serve_run(prec_fast, 8, 3, 8 * max(4, args.steps), None, 11)
+    _, srv_lat = serve_run(prec_fast, 8, 3, n_open, lam, 12)
+    plain_srv_fps, _ = serve_run("fp32", 1, 1, max(10, args.steps), None, 13)
+    _, plain_lat = serve_run("fp32", 1, 1, n_open, lam, 12)
+    clk = clocks.stop()
     r.set_precision(prec)
-    host_out = np.empty((B, H, W, 3), np.float32)
-    for i in range(2):
-        r.render_batch([pose(k) for k in range(B)], intr, W, H, NLEV, [FS[k % 2] for k in range(B)], out=host_out)
-    Ke = max(3, args.steps // 2)
-    t0 = time.perf_counter()
-    for i in range(Ke):
-        r.render_batch([pose(i * B + k) for k in range(B)], intr, W, H, NLEV,
-                       [FS[(i * B + k) % 2] for k in range(B)], out=host_out)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": B * Ke / e2e_s, "unit": "frames/s",
-           "h2d_bytes_per_step": B * (96 + 24 + 4), "d2h_bytes_per_step": int(host_out.nbytes)}
+    e2e = {"value": srv_fps, "unit": "frames/s", "path": "serving API (lnr_submit/lnr_poll), BF16, closed loop",
+           "h2d_bytes_per_step": 96 + 24 + 4, "d2h_bytes_per_step": W * H * 3 * 4, "step": "one request"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_sample(scene, views, weights)
+        cpu = cpu_sample(oracle_grid(scene), views, weights)
 
-    launches_per_step = 3 + 1 + 1 + NLEV + 2 * (2 * len(CH) - 1) + (0 if have_tc else 1)
+    launches_per_step = 3 + 1 + 1 + NLEV + 2 * (2 * len(CH) - 1) + (0 if have_tc else 1)  # cull, splat, resolve, upsample, convs
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -315,11 +357,16 @@ def main():
                        "n_levels": NLEV, "filter_strength": list(FS), "cell": CELL, "unet": list(CH),
                        "precision": prec, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2: per-step working set > 1 GB, every step new poses"},
-            "latency_ms": {"batched": {"p50": float(np.percentile(step_ms, 50)),
-                                       "p99": float(np.percentile(step_ms, 99))},
-                           "plain_fp32": {"p50": float(np.percentile(plain_ms, 50)),
-                                          "p99": float(np.percentile(plain_ms, 99))}},
-            "plain_fp32": {"value": plain_fps, "unit": "frames/s"},
+            "latency_ms": {"batched_step": {"p50": float(np.percentile(step_ms, 50)),
+                                            "p99": float(np.percentile(step_ms, 99))},
+                           "served_bf16": {"p50": float(np.percentile(srv_lat, 50)),
+                                           "p99": float(np.percentile(srv_lat, 99)),
+                                           "arrivals_per_s": lam, "requests": int(n_open)},
+                           "plain_fp32": {"p50": float(np.percentile(plain_lat, 50)),
+                                          "p99": float(np.percentile(plain_lat, 99)),
+                                          "arrivals_per_s": lam, "requests": int(n_open)}},
+            "plain_fp32": {"value": plain_fps, "unit": "frames/s", "served_value": plain_srv_fps},
+            "served_bf16": {"value": srv_fps, "unit": "frames/s"},
             "stages_ms_per_batch": {k: round(float(np.median([t[k] for t in tims])), 4)
                                     for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]},
             "grid_build_ms": grid_ms,
