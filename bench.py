@@ -181,6 +181,9 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time the batched path only (no stage timing, plain, serving or CPU legs): "
+                         "the command the ncu captures in profiles/ run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -257,6 +260,15 @@ def main():
         tot_ms = float(t.item())
     frames = B * args.steps * world
     value = frames / (tot_ms / 1e3)
+
+    if args.only_batched:
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+                              "mode": "only-batched", "config": {"views_per_step": B, "precision": prec}}))
+        r.close()
+        return
 
     # ---- stage timing of the batched path (dominant kernel) ------------------------
     r.set_timing(True)
