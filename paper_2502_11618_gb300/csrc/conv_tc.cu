@@ -420,6 +420,7 @@ struct HParams {
     HSeg seg[2];
     int nseg;
     int R, parity, W, H, B, N;  // parity: parity classes per tile (0 = standard tiles)
+    int wmax;                   // standard tiles: output rows per MMA (N = wmax * Cout <= 256)
     int tiles_x, tiles_y, ntiles;
     int stages;
     uint32_t stage_bytes, tmem_cols, idesc;
@@ -624,6 +625,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                     tc_fence_after();
                     const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
                     const uint32_t b0 = a0 + (s.b_off >> 4);
+                    if (PAR == 0) {
+                        // Halo row h shifted by kx feeds output rows r = h - ky, ky = 0..2.
+                        // Up to wmax consecutive rows go into one MMA: their accumulators
+                        // are adjacent in TMEM and their weight blocks [kx][ky = 2,1,0]
+                        // adjacent in shared memory, so N = rows * Cout.
+                        const int wmax = p.wmax;
+                        const uint32_t idesc0 = p.idesc & ~(0x3Fu << 17);
+                        for (int kx = 0; kx < 3; ++kx)
+                            for (int k = 0; k < nk; ++k) {
+                                const bool init = cc == 0 && kx == 0 && k == 0;  // first touch of every row
+                                for (int h = 0; h < R + 2; ++h) {
+                                    const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h < R - 1 ? h : R - 1;
+                                    const uint64_t ad = hi | (uint64_t)(a0 + h * row16 + kx * pitch16 + 2 * k);
+                                    if (init) {  // one row per MMA, zeroing each accumulator at ky = 0
+                                        for (int r = rlo; r <= rhi; ++r) {
+                                            const int blk = kx * 3 + (2 - (h - r));
+                                            mma_bf16(d0 + (uint32_t)(r * N), ad,
+                                                     hi | (uint64_t)(b0 + blk * btap + 2 * k), p.idesc, h == r ? 0u : 1u);
+                                        }
+                                        continue;
+                                    }
+                                    for (int r0 = rlo; r0 <= rhi; r0 += wmax) {
+                                        const int r1 = r0 + wmax - 1 < rhi ? r0 + wmax - 1 : rhi;
+                                        const int blk = kx * 3 + (2 - (h - r0));
+                                        const uint32_t nn = (uint32_t)((r1 - r0 + 1) * N);
+                                        mma_bf16(d0 + (uint32_t)(r0 * N), ad, hi | (uint64_t)(b0 + blk * btap + 2 * k),
+                                                 idesc0 | ((nn >> 3) << 17), 1u);
+                                    }
+                                }
+                            }
+                        first = 0;
+                    } else {
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
                         for (int k = 0; k < nk; ++k) {
@@ -639,6 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                             }
                             first = 0;
                         }
+                    }
                     }
                     issued = true;
                     mma_commit(empty(st));
@@ -948,7 +982,11 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
     for (int sg = 0; sg < nseg; ++sg) {
         const int ck = seg_ck(segC[sg], ckmax);
         for (int cc = 0; cc < segC[sg] / ck; ++cc)
-            for (int t = 0; t < 9; ++t)
+            for (int j = 0; j < 9; ++j) {
+                // standard convs: tap blocks ordered [kx][ky = 2, 1, 0], so that the blocks
+                // of one kx and consecutive output rows form one contiguous B operand;
+                // decoder concat convs: [ky][kx]
+                const int t = L.cin1 ? j : (2 - j % 3) * 3 + j / 3;
                 for (int n = 0; n < N; ++n)
                     for (int e = 0; e < ck; ++e) {
                         const int ch = segOff[sg] + cc * ck + e;  // padded channel
@@ -958,6 +996,7 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
                         const float v = src >= 0 ? L.wf[((size_t)n * cin + src) * 9 + t] : 0.f;
                         w.push_back(__float2bfloat16(v));
                     }
+            }
     }
     if (dst) cudaFree(dst);
     dst = nullptr;
@@ -1025,6 +1064,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * NC * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = P;
+    p.wmax = std::max(1, std::min(3, 256 / N));
     const cuuint64_t eb = 2;
     size_t w_off = 0;  // elements into wh
     uint32_t stage = 0;
