@@ -37,6 +37,11 @@ namespace lnr {
 namespace {
 
 constexpr int kThreads = 192;
+// halo kernel: producer warp, kMmaWarps MMA-issuing warps, 4 epilogue warps.  One thread
+// issues about one tcgen05.mma per ~120 cycles whatever N is, so small-N convolutions need
+// several issuing threads; each owns disjoint accumulators.
+constexpr int kMmaWarps = 4;
+constexpr int kHaloThreads = 32 * (1 + kMmaWarps + 4);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
 
@@ -421,6 +426,7 @@ struct HParams {
     int nseg;
     int R, parity, W, H, B, N;  // parity: parity classes per tile (0 = standard tiles)
     int wmax;                   // standard tiles: output rows per MMA (N = wmax * Cout <= 256)
+    int nmma;                   // MMA-issuing threads in use (<= kMmaWarps, <= accumulators per tile)
     int tiles_x, tiles_y, ntiles;
     int stages;
     uint32_t stage_bytes, tmem_cols, idesc;
@@ -481,7 +487,7 @@ __device__ __forceinline__ uint64_t sdesc_hi(uint32_t sbo, uint32_t swz) {
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
 // class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
 template <int R, int PAR>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
+__global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -502,19 +508,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
-            mbar_init(empty(s), 1);
+            mbar_init(empty(s), p.nmma);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(tfull(b), 1);
+            mbar_init(tfull(b), p.nmma);
             mbar_init(tempty(b), 4);
         }
-        mbar_init(drain, 1);
+        mbar_init(drain, p.nmma);
         *flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < N; i += kThreads) sbias[i] = p.bias[i];
+    for (int i = threadIdx.x; i < N; i += kHaloThreads) sbias[i] = p.bias[i];
     if (p.head_out)
-        for (int i = threadIdx.x; i < p.head_o * (N + 1); i += kThreads)
+        for (int i = threadIdx.x; i < p.head_o * (N + 1); i += kHaloThreads)
             shw[i] = i < p.head_o * N ? p.head_w[i] : p.head_b[i - p.head_o * N];
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
@@ -573,10 +579,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
         }
         if (!ok) atomicExch(p.err, 5);
         for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp >= 1 && warp <= kMmaWarps && lane == 0 && warp - 1 < p.nmma) {
         // ----------------------------------------------------------------- MMA --
+        // Issuer g owns accumulators [a_lo, a_hi] of every tile (a = class * R + row).
         // Descriptors are built once per stage; every tap, row and K step only adds a
         // constant to the start-address field (address >> 4, 14 bits).
+        constexpr int NCA = PAR == 0 ? 1 : PAR;
+        const int g = warp - 1, nacc = NCA * R;
+        const int a_lo = g * nacc / p.nmma, a_hi = (g + 1) * nacc / p.nmma - 1;
         int use = 0, tcount = 0;
         bool ok = true, issued = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
@@ -635,8 +645,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                         for (int kx = 0; kx < 3; ++kx)
                             for (int k = 0; k < nk; ++k) {
                                 const bool init = cc == 0 && kx == 0 && k == 0;  // first touch of every row
-                                for (int h = 0; h < R + 2; ++h) {
-                                    const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h < R - 1 ? h : R - 1;
+                                for (int h = a_lo; h < a_hi + 3; ++h) {
+                                    const int rlo = h - 2 > a_lo ? h - 2 : a_lo, rhi = h < a_hi ? h : a_hi;
                                     const uint64_t ad = hi | (uint64_t)(a0 + h * row16 + kx * pitch16 + 2 * k);
                                     if (init) {  // one row per MMA, zeroing each accumulator at ky = 0
                                         for (int r = rlo; r <= rhi; ++r) {
@@ -662,13 +672,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
                         for (int k = 0; k < nk; ++k) {
                             const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
                             const uint32_t acc = first ? 0u : 1u;
-#pragma unroll
-                            for (int c = 0; c < NC; ++c) {
-                                const uint32_t ab = a0 + off[c][tap] + 2 * k;
-#pragma unroll
-                                for (int r = 0; r < R; ++r)
-                                    mma_bf16(d0 + (uint32_t)((c * R + r) * N), hi | (uint64_t)(ab + r * rstep), bd, p.idesc,
-                                             acc);
+                            for (int a = a_lo; a <= a_hi; ++a) {
+                                const int c = a / R, r = a - c * R;
+                                mma_bf16(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off[c][tap] + 2 * k + r * rstep), bd,
+                                         p.idesc, acc);
                             }
                             first = 0;
                         }
@@ -682,15 +689,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_halo(const __grid_constant
             if (ok) mma_commit(tfull(b));
         }
         if (!ok) atomicExch(p.err, 6);
-        if (issued) {
-            mma_commit(drain);
-            mbar_wait(drain, 0);
-        }
-    } else if (warp >= 2) {
+        // every issuer arrives (the barrier counts them all); the wait makes sure every MMA
+        // issued has completed before TMEM is released
+        (void)issued;
+        mma_commit(drain);
+        mbar_wait(drain, 0);
+    } else if (warp > kMmaWarps) {
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
         const int m = 32 * q + lane;
-        const bool leader = threadIdx.x == 64;
+        const bool leader = threadIdx.x == 32 * (kMmaWarps + 1);
         const int Wh = p.W >> 1, Hh = p.H >> 1;
         const bool pool = p.pool_out != nullptr;
         int tcount = 0;
@@ -1065,6 +1073,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = P;
     p.wmax = std::max(1, std::min(3, 256 / N));
+    p.nmma = std::min(kMmaWarps, NC * R);
     const cuuint64_t eb = 2;
     size_t w_off = 0;  // elements into wh
     uint32_t stage = 0;
@@ -1153,7 +1162,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             if (done.insert((const void*)kern).second)
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
-        kern<<<grid, kThreads, smem, st>>>(p);
+        kern<<<grid, kHaloThreads, smem, st>>>(p);
     };
     auto pick = [&](auto par) {
         constexpr int PP = decltype(par)::value;
