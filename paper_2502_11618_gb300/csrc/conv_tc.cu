@@ -603,31 +603,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                 const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16;
                 const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
                 const int nk = s.ck >> 4;
-                const bool skip = PAR && sg == 0, coarse = PAR && sg == 1;
-                constexpr int NC = PAR == 0 ? 1 : PAR;  // parity classes in the tile
-                // per class and tap: offset (16-byte units) of output row 0; row step
-                uint32_t off[NC][9];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
-                    const int cpy = PAR == 4 ? (c >> 1) : py;
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int ky = tap / 3, kx = tap % 3;
-                        if (skip) {
-                            const int dxf = cpx + kx - 1;
-                            const int row = (PAR == 4 ? cpy : 0) + ky;  // staged fine row of output row 0
-                            off[c][tap] = (uint32_t)(dxf & 1) * (s.plane >> 4) + row * row16 +
-                                          (uint32_t)(1 + (dxf >> 1)) * pitch16;
-                        } else if (coarse) {
-                            off[c][tap] = (uint32_t)(1 + ((cpy + ky - 1) >> 1)) * row16 +
-                                          (uint32_t)(1 + ((cpx + kx - 1) >> 1)) * pitch16;
-                        } else {
-                            off[c][tap] = ky * row16 + kx * pitch16;
-                        }
-                    }
-                }
-                const uint32_t rstep = skip ? 2 * row16 : row16;
+                const bool skip = PAR && sg == 0;
+                const uint32_t plane16 = s.plane >> 4;
                 const uint32_t btap = (uint32_t)N * pitch16;
                 for (int cc = 0; cc < s.nchunk; ++cc) {
                     const int st = use % S;
@@ -637,9 +614,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     const uint32_t b0 = a0 + (s.b_off >> 4);
                     if (PAR == 0) {
                         // Halo row h shifted by kx feeds output rows r = h - ky, ky = 0..2.
-                        // Up to wmax consecutive rows go into one MMA: their accumulators
-                        // are adjacent in TMEM and their weight blocks [kx][ky = 2,1,0]
-                        // adjacent in shared memory, so N = rows * Cout.
+                        // Up to wmax consecutive rows of this issuer go into one MMA: their
+                        // accumulators are adjacent in TMEM and their weight blocks
+                        // [kx][ky = 2,1,0] adjacent in shared memory, so N = rows * Cout.
                         const int wmax = p.wmax;
                         const uint32_t idesc0 = p.idesc & ~(0x3Fu << 17);
                         for (int kx = 0; kx < 3; ++kx)
@@ -665,21 +642,32 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                     }
                                 }
                             }
-                        first = 0;
                     } else {
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        for (int k = 0; k < nk; ++k) {
-                            const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
-                            const uint32_t acc = first ? 0u : 1u;
-                            for (int a = a_lo; a <= a_hi; ++a) {
-                                const int c = a / R, r = a - c * R;
-                                mma_bf16(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off[c][tap] + 2 * k + r * rstep), bd,
-                                         p.idesc, acc);
+                        // decoder concat conv: accumulator a = class * R + row; the A tile of
+                        // (class, tap) is a shifted row of the staged skip planes or coarse rows
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const int ky = tap / 3, kx = tap - 3 * ky;
+                            for (int k = 0; k < nk; ++k) {
+                                const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
+                                const uint32_t acc = (cc | tap | k) ? 1u : 0u;
+                                for (int a = a_lo; a <= a_hi; ++a) {
+                                    const int c = a / R, r = a - c * R;
+                                    const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
+                                    const int cpy = PAR == 4 ? (c >> 1) : py;
+                                    uint32_t off;
+                                    if (skip) {
+                                        const int dxf = cpx + kx - 1;
+                                        off = (uint32_t)(dxf & 1) * plane16 + (uint32_t)((PAR == 4 ? cpy : 0) + ky + 2 * r) * row16 +
+                                              (uint32_t)(1 + (dxf >> 1)) * pitch16;
+                                    } else {
+                                        off = (uint32_t)(1 + r + ((cpy + ky - 1) >> 1)) * row16 +
+                                              (uint32_t)(1 + ((cpx + kx - 1) >> 1)) * pitch16;
+                                    }
+                                    mma_bf16(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off + 2 * k), bd, p.idesc,
+                                             (sg == 0) ? acc : 1u);
+                                }
                             }
-                            first = 0;
                         }
-                    }
                     }
                     issued = true;
                     mma_commit(empty(st));
@@ -1073,7 +1061,9 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = P;
     p.wmax = std::max(1, std::min(3, 256 / N));
-    p.nmma = std::min(kMmaWarps, NC * R);
+    // two issuers for standard tiles (each takes half the rows and windows within it), one
+    // per accumulator (up to four) for the parity classes of the decoder concat convs
+    p.nmma = P ? std::min(kMmaWarps, NC * R) : (R >= 2 ? 2 : 1);
     const cuuint64_t eb = 2;
     size_t w_off = 0;  // elements into wh
     uint32_t stage = 0;
