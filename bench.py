@@ -219,6 +219,9 @@ def main():
         r.set_unet(CH, weights, "fp32")
     prec = "bf16" if have_tc else "fp32"
     B = args.batch
+    t0 = time.perf_counter()
+    r.autotune(W, H, B)          # per-layer conv kernel choice (outside every timed region)
+    tune_s = time.perf_counter() - t0
     # every rank renders its own poses (replicas: views are independent)
     pose = lambda i: views[(i * 7 + rank * 3) % len(views)]
     out = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
@@ -382,6 +385,7 @@ def main():
             "stages_ms_per_batch": {k: round(float(np.median([t[k] for t in tims])), 4)
                                     for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]},
             "grid_build_ms": grid_ms,
+            "autotune_s": tune_s,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -134,6 +134,16 @@ lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
                             const lnr_intrinsics* intr, int W, int H, int n_levels,
                             const float* fs, float* out_rgb, int out_on_device);
 
+/* Autotune the tensor-core U-Net for batches of `batch` views at W x H (SURVEY-listed
+ * batching pattern; the paper has no counterpart): for every convolution, every valid
+ * kernel configuration (generic kernel; halo kernel over tile heights, parity classes per
+ * tile and K-chunk widths) is timed on the device and the fastest is kept for that layer
+ * resolution; later renders and served batches at that resolution use it.  Runs on the
+ * context's stream and waits for it.  Needs set_unet; a no-op for the FP32 precision.
+ * Errors: LNR_E_STATE before set_unet, LNR_E_ARG for sizes as lnr_render or batch outside
+ * [1, 64], LNR_E_OOM / LNR_E_CUDA. */
+lnr_status lnr_autotune(lnr_ctx* ctx, int W, int H, int batch);
+
 /* ---- serving: continuous batching of render requests ------------------------------ */
 
 /* Start the serving loop: up to max_batch requests of one resolution per launch, up to

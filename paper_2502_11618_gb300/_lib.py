@@ -25,7 +25,7 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
-           "lnr_filter_static"]
+           "lnr_filter_static", "lnr_autotune"]
 
 
 class LnrError(RuntimeError):
@@ -82,6 +82,7 @@ def lib():
             "lnr_set_timing": ([p, i], st),
             "lnr_get_timing": ([p, p], st),
             "lnr_filter_static": ([p, i, i, i, f, p, p], st),
+            "lnr_autotune": ([p, i, i, i], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -170,6 +171,10 @@ class Renderer:
         self._check(self._L.lnr_set_unet(self._c, C.byref(d), _ptr(w), w.size,
                                          PRECISIONS.get(precision, precision)))
         self.levels = len(ch)
+
+    def autotune(self, W, H, batch=1):
+        """Time every tensor-core conv configuration at (batch, W, H); keep the fastest."""
+        self._check(self._L.lnr_autotune(self._c, int(W), int(H), int(batch)))
 
     def set_precision(self, precision):
         self._check(self._L.lnr_set_precision(self._c, PRECISIONS.get(precision, precision)))

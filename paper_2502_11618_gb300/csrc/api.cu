@@ -571,6 +571,29 @@ lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsi
     return LNR_OK;
 }
 
+lnr_status lnr_autotune(lnr_ctx* c, int W, int H, int batch) {
+    if (!c) return LNR_E_ARG;
+    if (!c->unet_ok) return fail(c, LNR_E_STATE, "autotune before set_unet");
+    const int m = 1 << (c->unet.levels - 1);
+    if (W < m || H < m || W % m || H % m || batch < 1 || batch > 64 || (int64_t)W * H * batch > (1ll << 31))
+        return fail(c, LNR_E_ARG, "autotune: W, H must be multiples of 2^(levels-1); batch in [1, 64]");
+    if (c->prec == LNR_FP32) return LNR_OK;  // the FP32 path has one kernel per layer shape
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    cudaError_t e = cudaStreamSynchronize(ws.stream);
+    ws.B = batch;
+    ws.W = W;
+    ws.H = H;
+    const void* in_before = ws.act[4 * kMaxUnetLevels].p;
+    const void* out_before = ws.out.p;
+    if (!e) e = ws.act[4 * kMaxUnetLevels].ensure((size_t)batch * W * H * 8 * 4 + 256);
+    if (!e) e = ws.out.ensure((size_t)batch * W * H * 12);
+    if (!e) e = unet_ensure(c->unet, ws, LNR_FP32);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune buffers");
+    if (in_before != ws.act[4 * kMaxUnetLevels].p || out_before != ws.out.p) ws.alloc_gen++;
+    return unet_autotune(c, ws, c->prec, 3);
+}
+
 lnr_status lnr_set_timing(lnr_ctx* c, int enable) {
     if (!c) return LNR_E_ARG;
     c->timing = enable != 0;

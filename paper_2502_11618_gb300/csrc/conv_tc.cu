@@ -1174,21 +1174,62 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
 
 void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
              const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
-             cudaStream_t st) {
+             cudaStream_t st, const TcConfig* force) {
     (void)prec;
     tc_init();
     static const int forced = [] {
         const char* e = getenv("LNR_CONV_KERNEL");
         return (e && !strcmp(e, "generic")) ? 2 : (e && !strcmp(e, "halo")) ? 3 : 0;
     }();
-    int mode = forced == 3 ? 0 : forced ? forced : L.tc_mode;
-    if (mode == 0 && L.cout >= 256 && forced != 3) mode = 2;  // B traffic per 128-row tile favours the generic kernel there
-    if (mode != 2) {
-        int R = L.tc_R, P = L.tc_P, CK = L.tc_CK;
-        if (mode == 0) halo_default(L, R, P, CK);
+    TcConfig cfg;
+    if (force) {
+        cfg = *force;
+    } else if (!forced) {
+        auto it = L.tuned.find({W, H});
+        if (it != L.tuned.end()) cfg = it->second;
+        else if (L.cout >= 256) cfg.mode = 2;  // B traffic per 128-row tile favours the generic kernel there
+    } else if (forced == 2) {
+        cfg.mode = 2;
+    }
+    if (cfg.mode != 2) {
+        int R = cfg.R, P = cfg.P, CK = cfg.CK;
+        if (cfg.mode == 0) halo_default(L, R, P, CK);
         if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, st)) return;
     }
     tc_conv_generic(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, st);
+}
+
+// Every valid kernel configuration of a layer: the generic kernel, and the halo kernel over
+// tile heights, parity classes per tile and chunk widths that fit TMEM (double-buffered
+// accumulators) and at least two pipeline stages.
+std::vector<TcConfig> tc_candidates(const ConvLayer& L) {
+    std::vector<TcConfig> out;
+    TcConfig g;
+    g.mode = 2;
+    out.push_back(g);
+    const int N = L.cout;
+    const int Ps[3] = {1, 2, 4};
+    for (int r : {1, 2, 4, 8})
+        for (int pi = 0; pi < (L.cin1 ? 3 : 1); ++pi) {
+            const int P = L.cin1 ? Ps[pi] : 0, NC = P ? P : 1;
+            if (2 * NC * r * N > 512 || (L.pool && (r & 1))) continue;
+            int last_ck[2] = {-1, -1};
+            for (int ck : {16, 32, 64}) {
+                // skip chunk widths that give the same per-segment chunks as a smaller one
+                const int c0 = seg_ck(tc_c0(L), ck), c1 = L.cin1 ? seg_ck(L.cin1, ck) : 0;
+                if (c0 == last_ck[0] && c1 == last_ck[1]) continue;
+                last_ck[0] = c0;
+                last_ck[1] = c1;
+                if (halo_stage_bytes(L, r, P, ck) * 2 > 220u * 1024u) continue;
+                TcConfig c;
+                c.mode = 1;
+                c.R = r;
+                c.P = P;
+                c.CK = ck;
+                out.push_back(c);
+            }
+        }
+    return out;
 }
 
 int tc_error_word() {

@@ -35,6 +35,13 @@ struct ViewDev {
     float inv_pad;
 };
 
+// Tensor-core kernel choice for one convolution: mode 0 = built-in default, 1 = halo
+// kernel with (R, P, CK), 2 = generic kernel.
+struct TcConfig {
+    int mode = 0;
+    int R = 0, P = 0, CK = 0;
+};
+
 // One convolution as the GPU runs it.
 struct ConvLayer {
     int cin0 = 0;       // channels read from the same-resolution source
@@ -48,8 +55,7 @@ struct ConvLayer {
     float* b32 = nullptr;   // device, FP32 [cout]
     void* wtc = nullptr;    // device, tensor-core weights [cout][tap][cin_pad] (bf16 or fp8)
     void* wh[3] = {nullptr, nullptr, nullptr};  // device, halo-kernel weights for chunks of <= 16 / 32 / 64 channels
-    int tc_mode = 0;        // 0: halo kernel, default tile; 1: halo kernel, tc_R x tc_CK; 2: generic kernel
-    int tc_R = 0, tc_P = 0, tc_CK = 0;
+    std::map<std::pair<int, int>, TcConfig> tuned;  // autotuned kernel per layer resolution (W, H)
     float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null
     std::vector<float> wf;  // host FP32 OIHW after batch-norm folding
     std::vector<float> bf;
@@ -200,6 +206,7 @@ cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_gr
 size_t frame_bytes(int B, int W, int H);  // raster workspace bytes of a batch
 
 // unet.cu
+lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps);
 cudaError_t unet_ensure(const Unet& u, Workspace& ws, lnr_precision p);
 size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p);
 lnr_status unet_prepare(lnr_ctx* c);
@@ -212,7 +219,8 @@ bool tc_available();
 cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p);
 void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out,
              void* pool_out, const float* head_w, const float* head_b, float* head_out, int B,
-             int W, int H, int head_o, cudaStream_t st);
+             int W, int H, int head_o, cudaStream_t st, const TcConfig* force = nullptr);
+std::vector<TcConfig> tc_candidates(const ConvLayer& L);
 int tc_error_word();  // nonzero after a bounded wait in a tensor-core kernel ran out (then reset)
 
 }  // namespace lnr

@@ -8,6 +8,8 @@
 // GPU) and the layer orchestration shared by every precision.  Pooling, upsampling and
 // concatenation are fused into the convolutions: nothing but conv outputs is written.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "lnr_internal.h"
 
@@ -194,34 +196,33 @@ cudaError_t unet_ensure(const Unet& u, Workspace& ws, lnr_precision p) {
     return cudaSuccess;
 }
 
-void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
-                  cudaStream_t st, cudaEvent_t* layer_ev) {
-    const Unet& u = c->unet;
-    if (unet_ensure(u, ws, p) != cudaSuccess) return;
+// One convolution launch of the forward pass: layer, sources, outputs, resolution.
+struct ConvCall {
+    int layer;
+    const void* src0;
+    const void* src1;
+    void* out;
+    void* pool;
+    const float* head_w;
+    const float* head_b;
+    float* head_out;
+    int W, H;
+};
+
+// The forward pass as a list of convolution launches (encoder: conv, conv (+pool) per
+// level; decoder: concat conv, conv (+head on the last)); buffers from the workspace.
+static std::vector<ConvCall> unet_plan(const Unet& u, Workspace& ws, lnr_precision p, const void* in, float* out) {
+    std::vector<ConvCall> calls;
     const int L = u.levels;
     int ci = 0;
     const void* x = in;
-    int ev = 0;
-    auto mark = [&]() {
-        if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
-    };
-    mark();
     for (int l = 0; l < L; ++l) {
         const int W = ws.W >> l, H = ws.H >> l;
         void* t = ws.act[slot(l, 0)].p;
         void* s = ws.act[slot(l, 1)].p;
         void* pl = (l < L - 1) ? ws.act[slot(l, 2)].p : nullptr;
-        if (p == LNR_FP32) {
-            conv_f32(u.convs[ci], (const float*)x, nullptr, (float*)t, nullptr, ws.B, W, H, st);
-            mark();
-            conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)s, (float*)pl, ws.B, W, H, st);
-            mark();
-        } else {
-            tc_conv(u.convs[ci], p, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
-            mark();
-            tc_conv(u.convs[ci + 1], p, t, nullptr, s, pl, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
-            mark();
-        }
+        calls.push_back({ci, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, W, H});
+        calls.push_back({ci + 1, t, nullptr, s, pl, nullptr, nullptr, nullptr, W, H});
         ci += 2;
         x = pl;
     }
@@ -231,30 +232,88 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
         void* t = ws.act[slot(l, 0)].p;
         void* d = ws.act[slot(l, 3)].p;
         const void* skip = ws.act[slot(l, 1)].p;
-        if (p == LNR_FP32) {
-            conv_f32(u.convs[ci], (const float*)skip, (const float*)deep, (float*)t, nullptr, ws.B, W, H, st);
-            mark();
-            conv_f32(u.convs[ci + 1], (const float*)t, nullptr, (float*)d, nullptr, ws.B, W, H, st);
-            mark();
-        } else {
-            tc_conv(u.convs[ci], p, skip, deep, t, nullptr, nullptr, nullptr, nullptr, ws.B, W, H, u.out_ch, st);
-            mark();
-            const bool last = (l == 0);
-            tc_conv(u.convs[ci + 1], p, t, nullptr, d, nullptr, last ? u.head_w : nullptr,
-                    last ? u.head_b : nullptr, last ? out : nullptr, ws.B, W, H, u.out_ch, st);
-            mark();
-        }
+        calls.push_back({ci, skip, deep, t, nullptr, nullptr, nullptr, nullptr, W, H});
+        const bool fuse_head = (l == 0) && p != LNR_FP32;
+        calls.push_back({ci + 1, t, nullptr, d, nullptr, fuse_head ? u.head_w : nullptr, fuse_head ? u.head_b : nullptr,
+                         fuse_head ? out : nullptr, W, H});
         ci += 2;
         deep = d;
     }
-    if (L == 1) deep = ws.act[slot(0, 1)].p;
-    if (p == LNR_FP32 || L == 1) {
-        size_t npx = (size_t)ws.B * ws.W * ws.H;
-        if (p == LNR_FP32)
-            k_head_f32<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>((const float*)deep, u.ch[0], u.head_w, u.head_b,
-                                                                      u.out_ch, out, npx);
-        mark();
+    return calls;
+}
+
+static void run_call(const Unet& u, const ConvCall& k, Workspace& ws, lnr_precision p, cudaStream_t st,
+                     const TcConfig* force) {
+    const ConvLayer& L = u.convs[k.layer];
+    if (p == LNR_FP32)
+        conv_f32(L, (const float*)k.src0, (const float*)k.src1, (float*)k.out, (float*)k.pool, ws.B, k.W, k.H, st);
+    else
+        tc_conv(L, p, k.src0, k.src1, k.out, k.pool, k.head_w, k.head_b, k.head_out, ws.B, k.W, k.H, u.out_ch, st, force);
+}
+
+void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
+                  cudaStream_t st, cudaEvent_t* layer_ev) {
+    const Unet& u = c->unet;
+    if (unet_ensure(u, ws, p) != cudaSuccess) return;
+    int ev = 0;
+    if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
+    for (const ConvCall& k : unet_plan(u, ws, p, in, out)) {
+        run_call(u, k, ws, p, st, nullptr);
+        if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
     }
+    if (p == LNR_FP32) {
+        const void* deep = ws.act[slot(u.levels > 1 ? 0 : 0, u.levels > 1 ? 3 : 1)].p;
+        size_t npx = (size_t)ws.B * ws.W * ws.H;
+        k_head_f32<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>((const float*)deep, u.ch[0], u.head_w, u.head_b,
+                                                                  u.out_ch, out, npx);
+        if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
+    }
+}
+
+// Autotuner: for every tensor-core convolution of the forward pass at the workspace's
+// (B, W, H), time each candidate kernel configuration (CUDA events, `reps` launches after a
+// warm-up launch) on the layer's real buffers and keep the fastest for that layer
+// resolution.  Contents of the buffers do not matter: the kernels are data-independent.
+lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
+    Unet& u = c->unet;
+    if (p == LNR_FP32) return LNR_OK;
+    cudaError_t e = unet_ensure(u, ws, p);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune buffers");
+    cudaStream_t st = ws.stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const void* in = ws.act[4 * kMaxUnetLevels].p;
+    for (const ConvCall& k : unet_plan(u, ws, p, in, ws.out.as<float>())) {
+        ConvLayer& L = u.convs[k.layer];
+        float best = 1e30f;
+        TcConfig best_cfg;
+        for (const TcConfig& cfg : tc_candidates(L)) {
+            run_call(u, k, ws, p, st, &cfg);  // warm-up (and first-use set-up)
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r) run_call(u, k, ws, p, st, &cfg);
+            cudaEventRecord(e1, st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (tc_error_word()) continue;  // a configuration that failed is never chosen
+            if (ms < best) {
+                best = ms;
+                best_cfg = cfg;
+            }
+        }
+        if (e != cudaSuccess) break;
+        L.tuned[{k.W, k.H}] = best_cfg;
+        static const bool log = getenv("LNR_TUNE_LOG") != nullptr;
+        if (log)
+            fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d  %.1f us\n", k.layer, k.W, k.H, best_cfg.mode,
+                    best_cfg.R, best_cfg.P, best_cfg.CK, 1e3 * best / reps);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    c->unet_gen++;  // captured graphs hold the old kernel choices
+    return LNR_OK;
 }
 
 // Convert the host weights (already batch-norm folded) to the device layouts.

@@ -128,3 +128,24 @@ def test_bf16_each_conv_kernel(lnr, kernel):
     r = subprocess.run([sys.executable, "-c", _KERNEL_SCRIPT.format(root=root)], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_bf16_autotuned_kernels_meet_the_bars(lnr):
+    """After the autotuner picks a kernel per layer, the BF16 bars still hold."""
+    s = synth.multiroom_scene(n_points=500_000)
+    g = oracle.build_grid(s.xyz, s.rgb, s.scan_id, 0.25)
+    ch = (32, 64, 128, 256)
+    w = synth.unet_weights(ch, seed=2)
+    r = _renderer(lnr, s, 0.25, ch, w, "bf16")
+    W, H = 392, 216
+    r.autotune(W, H, 2)
+    intr = synth.intrinsics_for(W, H)
+    views = synth.random_poses(s, 2, seed=5)
+    ys = r.render_batch(views, intr, W, H, 4, 1.0)
+    for v, y in zip(views, ys):
+        ref = oracle.render(g, v, intr, W, H, 4, 1.0, w, ch)
+        assert np.abs(y - ref["y"]).max() <= BF16_MAXABS
+        assert psnr(y, ref["y"]) >= BF16_PSNR
+    with pytest.raises(lnr.LnrError):
+        r.autotune(390, 216, 2)
+    r.close()
