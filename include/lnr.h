@@ -108,7 +108,9 @@ lnr_status lnr_grid_info(lnr_ctx* ctx, double* out_g0, int32_t* out_dims);
 lnr_status lnr_set_unet(lnr_ctx* ctx, const lnr_unet_desc* desc, const float* weights,
                         size_t n_floats, lnr_precision precision);
 
-/* Select the U-Net precision for later renders (weights must be loaded). */
+/* Select the U-Net precision for later renders (weights must be loaded; LNR_FP8 also needs
+ * lnr_calibrate).  lnr_set_unet with LNR_FP8 loads the weights, selects BF16 and returns
+ * LNR_E_STATE until the net is calibrated. */
 lnr_status lnr_set_precision(lnr_ctx* ctx, lnr_precision precision);
 
 /* Render one frame (Fig. 1): cull, splat, filter (Fig. 2) with n_levels min-pool levels
@@ -133,6 +135,16 @@ lnr_status lnr_render_stage(lnr_ctx* ctx, const lnr_view* view, const lnr_intrin
 lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
                             const lnr_intrinsics* intr, int W, int H, int n_levels,
                             const float* fs, float* out_rgb, int out_on_device);
+
+/* Calibrate the FP8 (E4M3) U-Net on one view (after set_unet): the view is rendered with
+ * the BF16 U-Net, the largest magnitude of every convolution's output sets that tensor's
+ * static scale (amax / 448), and E4M3 weights with per-output-channel scales are built
+ * with the input scales folded in; accumulation stays FP32 (the paper states no precision;
+ * SURVEY precision pattern).  Afterwards lnr_set_precision(LNR_FP8) is allowed.  Arguments
+ * as lnr_render.  Errors: as lnr_render; LNR_E_ARG when a channel count of the net is not a
+ * multiple of 32. */
+lnr_status lnr_calibrate(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                         int H, int n_levels, float fs);
 
 /* Autotune the tensor-core U-Net for batches of `batch` views at W x H (SURVEY-listed
  * batching pattern; the paper has no counterpart): for every convolution, every valid

@@ -25,7 +25,7 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
-           "lnr_filter_static", "lnr_autotune"]
+           "lnr_filter_static", "lnr_autotune", "lnr_calibrate"]
 
 
 class LnrError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
             "lnr_get_timing": ([p, p], st),
             "lnr_filter_static": ([p, i, i, i, f, p, p], st),
             "lnr_autotune": ([p, i, i, i], st),
+            "lnr_calibrate": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -171,6 +172,11 @@ class Renderer:
         self._check(self._L.lnr_set_unet(self._c, C.byref(d), _ptr(w), w.size,
                                          PRECISIONS.get(precision, precision)))
         self.levels = len(ch)
+
+    def calibrate(self, view, intr, W, H, n_levels, fs):
+        """Static E4M3 scales from one BF16 frame; enables the FP8 precision."""
+        self._check(self._L.lnr_calibrate(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)), W, H,
+                                          n_levels, float(fs)))
 
     def autotune(self, W, H, batch=1):
         """Time every tensor-core conv configuration at (batch, W, H); keep the fastest."""

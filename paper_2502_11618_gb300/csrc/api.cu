@@ -307,6 +307,9 @@ lnr_status lnr_destroy(lnr_ctx* c) {
         if (L.wtc) cudaFree(L.wtc);
         for (void* w : L.wh)
             if (w) cudaFree(w);
+        for (void* w : L.wh8)
+            if (w) cudaFree(w);
+        if (L.wscale8) cudaFree(L.wscale8);
         if (L.wscale) cudaFree(L.wscale);
     }
     if (c->unet.head_w) cudaFree(c->unet.head_w);
@@ -415,6 +418,9 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
         if (Lr.wtc) cudaFree(Lr.wtc);
         for (void* w : Lr.wh)
             if (w) cudaFree(w);
+        for (void* w : Lr.wh8)
+            if (w) cudaFree(w);
+        if (Lr.wscale8) cudaFree(Lr.wscale8);
         if (Lr.wscale) cudaFree(Lr.wscale);
     }
     Unet u;
@@ -468,9 +474,13 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
     c->unet_ok = true;
     c->prec = prec;
     c->unet_gen++;
-    if ((prec != LNR_FP32 && !tc_available()) || prec == LNR_FP8 || (prec != LNR_FP32 && L < 2)) {
+    if ((prec != LNR_FP32 && !tc_available()) || (prec != LNR_FP32 && L < 2)) {
         c->prec = LNR_FP32;
         return fail(c, LNR_E_ARG, "precision not available for this net in this build");
+    }
+    if (prec == LNR_FP8) {  // E4M3 needs calibrated activation scales first
+        c->prec = LNR_BF16;
+        return fail(c, LNR_E_STATE, "FP8 needs lnr_calibrate after set_unet (BF16 selected meanwhile)");
     }
     return LNR_OK;
 }
@@ -479,8 +489,9 @@ lnr_status lnr_set_precision(lnr_ctx* c, lnr_precision prec) {
     if (!c) return LNR_E_ARG;
     if (!c->unet_ok) return fail(c, LNR_E_STATE, "set_precision before set_unet");
     if (prec < LNR_FP32 || prec > LNR_FP8) return fail(c, LNR_E_ARG, "bad precision");
-    if ((prec != LNR_FP32 && !tc_available()) || prec == LNR_FP8 || (prec != LNR_FP32 && c->unet.levels < 2))
+    if ((prec != LNR_FP32 && !tc_available()) || (prec != LNR_FP32 && c->unet.levels < 2))
         return fail(c, LNR_E_ARG, "precision not available for this net in this build");
+    if (prec == LNR_FP8 && !c->unet.fp8_ready) return fail(c, LNR_E_STATE, "FP8 needs lnr_calibrate first");
     c->prec = prec;
     return LNR_OK;
 }
@@ -569,6 +580,24 @@ lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsi
     if (!e) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "render_stage");
     return LNR_OK;
+}
+
+lnr_status lnr_calibrate(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev, float fs) {
+    if (!c) return LNR_E_ARG;
+    lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, true);
+    if (s != LNR_OK) return s;
+    if (c->prec == LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "no tensor-core path in this build");
+    for (const auto& L : c->unet.convs)
+        if (L.cout < 32 || (L.cin0 != 5 && L.cin0 % 32) || L.cin1 % 32)
+            return fail(c, LNR_E_ARG, "FP8 needs every U-Net channel count to be a multiple of 32");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    if (s != LNR_OK) return s;
+    enqueue_frame(c, ws, ws.stream, -1, LNR_BF16, false);
+    cudaError_t e = cudaStreamSynchronize(ws.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "calibration frame");
+    return unet_calibrate_fp8(c, ws);
 }
 
 lnr_status lnr_autotune(lnr_ctx* c, int W, int H, int batch) {

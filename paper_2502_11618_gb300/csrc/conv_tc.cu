@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cstdlib>
 #include <type_traits>
@@ -141,6 +142,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+__device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+template <bool IN8>
+__device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (IN8) mma_fp8(d, a, b, idesc, acc);
+    else mma_bf16(d, a, b, idesc, acc);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -431,8 +443,11 @@ struct HParams {
     int stages;
     uint32_t stage_bytes, tmem_cols, idesc;
     const float* bias;
-    __nv_bfloat16* out;
-    __nv_bfloat16* pool_out;
+    const float* cscale;        // per-output-channel accumulator scale (FP8 operands), or null
+    void* out;                  // NHWC output, BF16 or (out_fp8) E4M3
+    void* pool_out;             // 2x2 max-pooled output, same type, or null
+    int out_fp8;
+    float inv_out;              // E4M3 output: value * inv_out is stored
     const float* head_w;
     const float* head_b;
     float* head_out;
@@ -445,6 +460,16 @@ __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint3
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
+}
+
+// 16 channels of one pixel: BF16 (32 bytes) or E4M3 of v * inv (16 bytes, saturating).
+__device__ __forceinline__ void st_fp8x16(uint8_t* dst, const float* v, float inv) {
+    uint4 pk;
+    uint16_t* ph = reinterpret_cast<uint16_t*>(&pk);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        ph[j] = __nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * inv, v[2 * j + 1] * inv), __NV_SATFINITE, __NV_E4M3);
+    *reinterpret_cast<uint4*>(dst) = pk;
 }
 
 __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
@@ -486,7 +511,7 @@ __device__ __forceinline__ uint64_t sdesc_hi(uint32_t sbo, uint32_t swz) {
 // conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
 // class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
-template <int R, int PAR>
+template <int R, int PAR, bool IN8>
 __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -502,7 +527,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
     float* sbias = reinterpret_cast<float*>(gbase + (tslot - base) + 16);
-    float* shw = sbias + p.N;             // head weights [head_o][N], then head bias
+    float* sscale = sbias + p.N;          // accumulator scale per output channel
+    float* shw = sscale + p.N;            // head weights [head_o][N], then head bias
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
     if (threadIdx.x == 0) {
@@ -518,7 +544,10 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         *flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < N; i += kHaloThreads) sbias[i] = p.bias[i];
+    for (int i = threadIdx.x; i < N; i += kHaloThreads) {
+        sbias[i] = p.bias[i];
+        sscale[i] = p.cscale ? p.cscale[i] : 1.0f;
+    }
     if (p.head_out)
         for (int i = threadIdx.x; i < p.head_o * (N + 1); i += kHaloThreads)
             shw[i] = i < p.head_o * N ? p.head_w[i] : p.head_b[i - p.head_o * N];
@@ -602,7 +631,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                 const HSeg& s = p.seg[sg];
                 const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16;
                 const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
-                const int nk = s.ck >> 4;
+                const int nk = (int)(s.pitch >> 5);  // one MMA per 32 bytes of K (16 BF16 or 32 E4M3)
                 const bool skip = PAR && sg == 0;
                 const uint32_t plane16 = s.plane >> 4;
                 const uint32_t btap = (uint32_t)N * pitch16;
@@ -628,7 +657,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                     if (init) {  // one row per MMA, zeroing each accumulator at ky = 0
                                         for (int r = rlo; r <= rhi; ++r) {
                                             const int blk = kx * 3 + (2 - (h - r));
-                                            mma_bf16(d0 + (uint32_t)(r * N), ad,
+                                            mma_op<IN8>(d0 + (uint32_t)(r * N), ad,
                                                      hi | (uint64_t)(b0 + blk * btap + 2 * k), p.idesc, h == r ? 0u : 1u);
                                         }
                                         continue;
@@ -637,7 +666,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                         const int r1 = r0 + wmax - 1 < rhi ? r0 + wmax - 1 : rhi;
                                         const int blk = kx * 3 + (2 - (h - r0));
                                         const uint32_t nn = (uint32_t)((r1 - r0 + 1) * N);
-                                        mma_bf16(d0 + (uint32_t)(r0 * N), ad, hi | (uint64_t)(b0 + blk * btap + 2 * k),
+                                        mma_op<IN8>(d0 + (uint32_t)(r0 * N), ad, hi | (uint64_t)(b0 + blk * btap + 2 * k),
                                                  idesc0 | ((nn >> 3) << 17), 1u);
                                     }
                                 }
@@ -663,7 +692,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                         off = (uint32_t)(1 + r + ((cpy + ky - 1) >> 1)) * row16 +
                                               (uint32_t)(1 + ((cpx + kx - 1) >> 1)) * pitch16;
                                     }
-                                    mma_bf16(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off + 2 * k), bd, p.idesc,
+                                    mma_op<IN8>(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off + 2 * k), bd, p.idesc,
                                              (sg == 0) ? acc : 1u);
                                 }
                             }
@@ -715,16 +744,24 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         float f0[16], f1[16], pm[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float bj = sbias[c0 + j];
-                            f0[j] = fmaxf(__uint_as_float(u0[j]) + bj, 0.f);
-                            f1[j] = fmaxf(__uint_as_float(u1[j]) + bj, 0.f);
+                            const float bj = sbias[c0 + j], sj = sscale[c0 + j];
+                            f0[j] = fmaxf(fmaf(__uint_as_float(u0[j]), sj, bj), 0.f);
+                            f1[j] = fmaxf(fmaf(__uint_as_float(u1[j]), sj, bj), 0.f);
                             const float a = fmaxf(f0[j], f1[j]);
                             pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                         }
-                        if (v0) st_bf16x16(p.out + (((size_t)n * p.H + y) * p.W + x) * N + c0, f0);
-                        if (v1) st_bf16x16(p.out + (((size_t)n * p.H + y + 1) * p.W + x) * N + c0, f1);
-                        if ((m & 1) == 0 && v1)
-                            st_bf16x16(p.pool_out + (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N + c0, pm);
+                        const size_t e0 = (((size_t)n * p.H + y) * p.W + x) * N + c0;
+                        const size_t e1 = e0 + (size_t)p.W * N;
+                        const size_t ep = (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N + c0;
+                        if (p.out_fp8) {
+                            if (v0) st_fp8x16(static_cast<uint8_t*>(p.out) + e0, f0, p.inv_out);
+                            if (v1) st_fp8x16(static_cast<uint8_t*>(p.out) + e1, f1, p.inv_out);
+                            if ((m & 1) == 0 && v1) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + ep, pm, p.inv_out);
+                        } else {
+                            if (v0) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e0, f0);
+                            if (v1) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e1, f1);
+                            if ((m & 1) == 0 && v1) st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
+                        }
                     }
                 }
             } else {
@@ -755,8 +792,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         float f0[16], f1[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            f0[j] = fmaxf(__uint_as_float(u0[j]) + sbias[c0 + j], 0.f);
-                            f1[j] = two ? fmaxf(__uint_as_float(u1[j]) + sbias[c0 + 16 + j], 0.f) : 0.f;
+                            f0[j] = fmaxf(fmaf(__uint_as_float(u0[j]), sscale[c0 + j], sbias[c0 + j]), 0.f);
+                            f1[j] = two ? fmaxf(fmaf(__uint_as_float(u1[j]), sscale[c0 + 16 + j], sbias[c0 + 16 + j]), 0.f)
+                                        : 0.f;
                         }
                         if (p.head_out) {
                             for (int o = 0; o < p.head_o; ++o) {
@@ -769,8 +807,13 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                 h[o] += sacc;
                             }
                         } else if (v) {
-                            st_bf16x16(p.out + pix * N + c0, f0);
-                            if (two) st_bf16x16(p.out + pix * N + c0 + 16, f1);
+                            if (p.out_fp8) {
+                                st_fp8x16(static_cast<uint8_t*>(p.out) + pix * N + c0, f0, p.inv_out);
+                                if (two) st_fp8x16(static_cast<uint8_t*>(p.out) + pix * N + c0 + 16, f1, p.inv_out);
+                            } else {
+                                st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0, f0);
+                                if (two) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0 + 16, f1);
+                            }
                         }
                     }
                     if (p.head_out && v)
@@ -819,6 +862,10 @@ int seg_ck(int C, int ckmax) {
     return ck;
 }
 
+CUtensorMapSwizzle swizzle_pitch(uint32_t pitch) {
+    return pitch == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : pitch == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+
 CUtensorMapSwizzle swizzle_for(int kc) {
     return kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
 }
@@ -845,7 +892,7 @@ bool tc_available() { return true; }
 // padded to 16 so that every K chunk is one 32-byte MMA step).
 static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 16 : L.cin0; }
 
-static cudaError_t prepare_halo_weights(ConvLayer& L, int CK);
+static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax);
 
 cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p) {
     if (p != LNR_BF16) return cudaErrorNotSupported;
@@ -967,21 +1014,21 @@ static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 
 
 // Weights of the halo kernel for chunks of at most ckmax channels: every K segment's
-// chunks in turn, each chunk [tap][N][ck] with ck = min(C_segment, ckmax) -- one TMA box
-// {ck, N, 9} per chunk, swizzled like the halo rows.
-static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
-    void*& dst = L.wh[ck_index(ckmax)];
-    const int c0 = tc_c0(L), cin = L.cin0 + L.cin1, N = L.cout;
+// chunks in turn, each chunk [tap][N][ck] with ck = seg_ck(C_segment, ckmax) -- one TMA box
+// {ck, N, 9} per chunk, swizzled like the halo rows.  Standard convs store their tap blocks
+// as [kx][ky = 2, 1, 0] (the blocks of one kx and consecutive output rows then form one
+// contiguous B operand); decoder concat convs as [ky][kx].  value(n, src, t) gives the
+// weight of output n, original input channel src, tap t; enc(v) its stored bytes.
+template <class T, class Value, class Enc>
+static cudaError_t halo_weights(const ConvLayer& L, int ckmax, Value value, Enc enc, void*& dst) {
+    const int c0 = tc_c0(L), N = L.cout;
     const int segC[2] = {c0, L.cin1}, segOff[2] = {0, c0};
     const int nseg = L.cin1 ? 2 : 1;
-    std::vector<__nv_bfloat16> w;
+    std::vector<T> w;
     for (int sg = 0; sg < nseg; ++sg) {
         const int ck = seg_ck(segC[sg], ckmax);
         for (int cc = 0; cc < segC[sg] / ck; ++cc)
             for (int j = 0; j < 9; ++j) {
-                // standard convs: tap blocks ordered [kx][ky = 2, 1, 0], so that the blocks
-                // of one kx and consecutive output rows form one contiguous B operand;
-                // decoder concat convs: [ky][kx]
                 const int t = L.cin1 ? j : (2 - j % 3) * 3 + j / 3;
                 for (int n = 0; n < N; ++n)
                     for (int e = 0; e < ck; ++e) {
@@ -989,27 +1036,62 @@ static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
                         int src;
                         if (ch < c0) src = ch < L.cin0 ? ch : -1;
                         else src = L.cin0 + (ch - c0);
-                        const float v = src >= 0 ? L.wf[((size_t)n * cin + src) * 9 + t] : 0.f;
-                        w.push_back(__float2bfloat16(v));
+                        w.push_back(enc(src >= 0 ? value(n, src, t) : 0.f));
                     }
             }
     }
     if (dst) cudaFree(dst);
     dst = nullptr;
-    cudaError_t e = cudaMalloc(&dst, w.size() * 2);
+    cudaError_t e = cudaMalloc(&dst, w.size() * sizeof(T));
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(dst, w.data(), w.size() * 2, cudaMemcpyHostToDevice);
+    return cudaMemcpy(dst, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
+    const int cin = L.cin0 + L.cin1;
+    return halo_weights<__nv_bfloat16>(
+        L, ckmax, [&](int n, int src, int t) { return L.wf[((size_t)n * cin + src) * 9 + t]; },
+        [](float v) { return __float2bfloat16(v); }, L.wh[ck_index(ckmax)]);
+}
+
+// E4M3 weights of an FP8 layer: w * (scale of the input segment the channel comes from),
+// divided by a per-output-channel scale so that each channel's largest |w| maps to 448.
+cudaError_t tc_prepare_fp8(ConvLayer& L) {
+    const int cin = L.cin0 + L.cin1, N = L.cout;
+    std::vector<float> sw(N, 0.f);
+    auto scaled = [&](int n, int src, int t) {
+        return L.wf[((size_t)n * cin + src) * 9 + t] * (src < L.cin0 ? L.in_scale[0] : L.in_scale[1]);
+    };
+    for (int n = 0; n < N; ++n) {
+        float m = 0.f;
+        for (int src = 0; src < cin; ++src)
+            for (int t = 0; t < 9; ++t) m = std::max(m, std::fabs(scaled(n, src, t)));
+        sw[n] = std::max(m, 1e-30f) / 448.0f;
+    }
+    cudaError_t e;
+    for (int i = 0; i < 3; ++i) {
+        const int ck = 32 << i;
+        e = halo_weights<__nv_fp8_storage_t>(
+            L, ck, [&](int n, int src, int t) { return scaled(n, src, t) / sw[n]; },
+            [](float v) { return __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }, L.wh8[i]);
+        if (e != cudaSuccess) return e;
+    }
+    if (L.wscale8) cudaFree(L.wscale8);
+    L.wscale8 = nullptr;
+    if ((e = cudaMalloc(&L.wscale8, 4 * N)) != cudaSuccess) return e;
+    L.fp8 = true;
+    return cudaMemcpy(L.wscale8, sw.data(), 4 * N, cudaMemcpyHostToDevice);
 }
 
 // Bytes of one pipeline stage of the halo kernel for a layer at tile height R, P parity
 // classes per tile (decoder concat convs) and chunks of at most ckmax channels.
-static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax) {
+static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, int esize = 2) {
     const int segC[2] = {tc_c0(L), L.cin1};
     uint32_t st = 0;
     for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg) {
         const int ck = seg_ck(segC[sg], ckmax);
         const int kind1 = L.cin1 && sg == 0;
-        const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = 2 * ck;
+        const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + 9u * L.cout * pitch, 1024));
     }
@@ -1046,11 +1128,21 @@ void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
     ckmax = 16;
 }
 
+// Element encoding of one halo-kernel launch: BF16 or E4M3 operands, BF16 or E4M3 output.
+struct HaloTypes {
+    bool in8 = false, out8 = false;
+    float inv_out = 1.f;
+    const float* cscale = nullptr;
+};
+
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
-                  int P, int ckmax, cudaStream_t st) {
-    const __nv_bfloat16* wh = static_cast<const __nv_bfloat16*>(L.wh[ck_index(ckmax)]);
-    if (!wh) return false;
+                  int P, int ckmax, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
+    const int esize = ty.in8 ? 1 : 2;
+    if (ty.in8 && ckmax < 32) return false;
+    const void* whp = ty.in8 ? L.wh8[ckmax == 32 ? 0 : ckmax == 64 ? 1 : 2] : L.wh[ck_index(ckmax)];
+    if (!whp) return false;
+    const uint8_t* wh = static_cast<const uint8_t*>(whp);
     HParams p;
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout, c0 = tc_c0(L);
@@ -1064,14 +1156,15 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     // two issuers for standard tiles (each takes half the rows and windows within it), one
     // per accumulator (up to four) for the parity classes of the decoder concat convs
     p.nmma = P ? std::min(kMmaWarps, NC * R) : (R >= 2 ? 2 : 1);
-    const cuuint64_t eb = 2;
-    size_t w_off = 0;  // elements into wh
+    const cuuint64_t eb = (cuuint64_t)esize;
+    const CUtensorMapDataType dt = ty.in8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    size_t w_off = 0;  // bytes into wh
     uint32_t stage = 0;
     auto set_seg = [&](HSeg& s, int kind, const void* src, int C, int Ws, int Hs) -> bool {
         s.kind = kind;
         s.ck = seg_ck(C, ckmax);
-        s.pitch = (uint32_t)s.ck * 2;
-        s.swz = umma_layout_for(s.ck);
+        s.pitch = (uint32_t)s.ck * esize;
+        s.swz = s.pitch == 128 ? 2u : s.pitch == 64 ? 4u : 6u;
         s.rows = kind == 1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2;
         s.nchunk = C / s.ck;
         const uint32_t planes = kind == 1 ? 2 : 1;
@@ -1087,24 +1180,24 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             cuuint64_t dims[5] = {(cuuint64_t)C, 2, (cuuint64_t)Ws / 2, (cuuint64_t)Hs, (cuuint64_t)B};
             cuuint64_t str[4] = {C * eb, 2 * C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
             cuuint32_t box[5] = {(cuuint32_t)s.ck, 1, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-            ok = encode_tiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(src), dims, str, box, es,
-                                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            ok = encode_tiled(&s.a, dt, 5, const_cast<void*>(src), dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         } else {
             cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
             cuuint64_t str[3] = {C * eb, (cuuint64_t)Ws * C * eb, (cuuint64_t)Hs * Ws * C * eb};
             cuuint32_t box[4] = {(cuuint32_t)s.ck, (cuuint32_t)kHaloW, (cuuint32_t)s.rows, 1};
-            ok = encode_tiled(&s.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(src), dims, str, box, es,
-                                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            ok = encode_tiled(&s.a, dt, 4, const_cast<void*>(src), dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
         cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)9 * s.nchunk};
         cuuint64_t wstr[2] = {s.ck * eb, (cuuint64_t)N * s.ck * eb};
         cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, 9};
-        ok = ok && encode_tiled(&s.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(wh + w_off),
-                                          wd, wstr, wbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(s.ck),
-                                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        w_off += (size_t)s.nchunk * 9 * N * s.ck;
+        ok = ok && encode_tiled(&s.b, dt, 3, const_cast<uint8_t*>(wh + w_off), wd, wstr, wbox, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        w_off += (size_t)s.nchunk * 9 * N * s.ck * esize;
         return ok;
     };
     bool ok;
@@ -1124,6 +1217,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     }
     p.stage_bytes = stage;
     p.stages = std::min<int>(8, (int)((220u * 1024u) / p.stage_bytes));
+    (void)halo_stage_bytes;
     if (p.stages < 2) return false;
     if (!ok) {
         g_host_err = 4;
@@ -1132,17 +1226,22 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     uint32_t cols = 32;
     while (cols < 2u * NC * R * N) cols <<= 1;
     p.tmem_cols = cols;
-    p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // D = FP32; operands BF16 (format 1, kind::f16) or E4M3 (format 0, kind::f8f6f4)
+    p.idesc = (1u << 4) | (ty.in8 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(N >> 3) << 17) |
+              ((uint32_t)(128 >> 4) << 24);
     p.bias = L.b32;
-    p.out = static_cast<__nv_bfloat16*>(out);
-    p.pool_out = static_cast<__nv_bfloat16*>(pool_out);
+    p.cscale = ty.cscale;
+    p.out = out;
+    p.pool_out = pool_out;
+    p.out_fp8 = ty.out8;
+    p.inv_out = ty.inv_out;
     p.head_w = head_w;
     p.head_b = head_b;
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 +
-                        4 * (size_t)(N + head_o * (N + 1));
+                        4 * (size_t)(2 * N + head_o * (N + 1));
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams)) {
         static std::mutex mu;
@@ -1156,11 +1255,20 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     };
     auto pick = [&](auto par) {
         constexpr int PP = decltype(par)::value;
-        switch (R) {
-            case 1: launch(k_conv_halo<1, PP>); break;
-            case 2: launch(k_conv_halo<2, PP>); break;
-            case 4: launch(k_conv_halo<4, PP>); break;
-            default: launch(k_conv_halo<8, PP>); break;
+        if (ty.in8) {
+            switch (R) {
+                case 1: launch(k_conv_halo<1, PP, true>); break;
+                case 2: launch(k_conv_halo<2, PP, true>); break;
+                case 4: launch(k_conv_halo<4, PP, true>); break;
+                default: launch(k_conv_halo<8, PP, true>); break;
+            }
+        } else {
+            switch (R) {
+                case 1: launch(k_conv_halo<1, PP, false>); break;
+                case 2: launch(k_conv_halo<2, PP, false>); break;
+                case 4: launch(k_conv_halo<4, PP, false>); break;
+                default: launch(k_conv_halo<8, PP, false>); break;
+            }
         }
     };
     switch (P) {
@@ -1175,26 +1283,42 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
 void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
              const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
              cudaStream_t st, const TcConfig* force) {
-    (void)prec;
     tc_init();
     static const int forced = [] {
         const char* e = getenv("LNR_CONV_KERNEL");
         return (e && !strcmp(e, "generic")) ? 2 : (e && !strcmp(e, "halo")) ? 3 : 0;
     }();
+    const bool fp8 = prec == LNR_FP8;
+    HaloTypes ty;
+    if (fp8) {
+        ty.in8 = L.fp8;
+        ty.out8 = head_out == nullptr;
+        ty.inv_out = 1.0f / L.out_scale;
+        ty.cscale = L.fp8 ? L.wscale8 : nullptr;
+    }
     TcConfig cfg;
+    const auto& table = fp8 ? L.tuned8 : L.tuned;
     if (force) {
         cfg = *force;
-    } else if (!forced) {
-        auto it = L.tuned.find({W, H});
-        if (it != L.tuned.end()) cfg = it->second;
-        else if (L.cout >= 256) cfg.mode = 2;  // B traffic per 128-row tile favours the generic kernel there
+    } else if (!forced || fp8) {
+        auto it = table.find({W, H});
+        if (it != table.end()) cfg = it->second;
+        else if (L.cout >= 256 && !fp8) cfg.mode = 2;  // B traffic per 128-row tile favours the generic kernel there
     } else if (forced == 2) {
         cfg.mode = 2;
     }
+    if (fp8 && cfg.mode == 2) cfg.mode = 0;  // the generic kernel is BF16 only
     if (cfg.mode != 2) {
         int R = cfg.R, P = cfg.P, CK = cfg.CK;
-        if (cfg.mode == 0) halo_default(L, R, P, CK);
-        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, st)) return;
+        if (cfg.mode == 0) {
+            halo_default(L, R, P, CK);
+            if (ty.in8) CK = std::max(32, CK);
+        }
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, st, ty)) return;
+        if (fp8) {  // no fallback for FP8: record and skip
+            g_host_err = 8;
+            return;
+        }
     }
     tc_conv_generic(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, st);
 }
@@ -1202,25 +1326,29 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
 // Every valid kernel configuration of a layer: the generic kernel, and the halo kernel over
 // tile heights, parity classes per tile and chunk widths that fit TMEM (double-buffered
 // accumulators) and at least two pipeline stages.
-std::vector<TcConfig> tc_candidates(const ConvLayer& L) {
+std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
     std::vector<TcConfig> out;
-    TcConfig g;
-    g.mode = 2;
-    out.push_back(g);
-    const int N = L.cout;
+    const bool in8 = prec == LNR_FP8 && L.fp8;
+    if (prec != LNR_FP8) {
+        TcConfig g;
+        g.mode = 2;
+        out.push_back(g);
+    }
+    const int N = L.cout, esize = in8 ? 1 : 2;
     const int Ps[3] = {1, 2, 4};
     for (int r : {1, 2, 4, 8})
         for (int pi = 0; pi < (L.cin1 ? 3 : 1); ++pi) {
             const int P = L.cin1 ? Ps[pi] : 0, NC = P ? P : 1;
             if (2 * NC * r * N > 512 || (L.pool && (r & 1))) continue;
             int last_ck[2] = {-1, -1};
-            for (int ck : {16, 32, 64}) {
+            for (int ck : {16, 32, 64, 128}) {
+                if (ck * esize > 128 || (in8 && ck < 32)) continue;
                 // skip chunk widths that give the same per-segment chunks as a smaller one
                 const int c0 = seg_ck(tc_c0(L), ck), c1 = L.cin1 ? seg_ck(L.cin1, ck) : 0;
                 if (c0 == last_ck[0] && c1 == last_ck[1]) continue;
                 last_ck[0] = c0;
                 last_ck[1] = c1;
-                if (halo_stage_bytes(L, r, P, ck) * 2 > 220u * 1024u) continue;
+                if (halo_stage_bytes(L, r, P, ck, esize) * 2 > 220u * 1024u) continue;
                 TcConfig c;
                 c.mode = 1;
                 c.R = r;

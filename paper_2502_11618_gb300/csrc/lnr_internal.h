@@ -56,6 +56,15 @@ struct ConvLayer {
     void* wtc = nullptr;    // device, tensor-core weights [cout][tap][cin_pad] (bf16 or fp8)
     void* wh[3] = {nullptr, nullptr, nullptr};  // device, halo-kernel weights for chunks of <= 16 / 32 / 64 channels
     std::map<std::pair<int, int>, TcConfig> tuned;  // autotuned kernel per layer resolution (W, H)
+    std::map<std::pair<int, int>, TcConfig> tuned8; // the same for the FP8 precision
+    // FP8 (E4M3): set by calibration.  Operands are E4M3 when fp8 (every conv but the
+    // first, whose input is the BF16 RGBDA image); in_scale: activation scale of each K
+    // segment's input; out_scale: of this conv's output; wscale8: per output channel.
+    bool fp8 = false;
+    float in_scale[2] = {1.f, 1.f};
+    float out_scale = 1.f;
+    void* wh8[3] = {nullptr, nullptr, nullptr};
+    float* wscale8 = nullptr;
     float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null
     std::vector<float> wf;  // host FP32 OIHW after batch-norm folding
     std::vector<float> bf;
@@ -69,7 +78,7 @@ struct Unet {
     float* head_w = nullptr;        // device FP32 [out_ch][ch0]
     float* head_b = nullptr;
     std::vector<float> head_wh, head_bh;
-    std::vector<float> act_scale;   // per conv: FP8 activation scale of its input
+    bool fp8_ready = false;         // FP8 weights and activation scales calibrated
 };
 
 // Grow-only device buffer.
@@ -207,6 +216,7 @@ size_t frame_bytes(int B, int W, int H);  // raster workspace bytes of a batch
 
 // unet.cu
 lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps);
+lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws);
 cudaError_t unet_ensure(const Unet& u, Workspace& ws, lnr_precision p);
 size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p);
 lnr_status unet_prepare(lnr_ctx* c);
@@ -220,7 +230,8 @@ cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p);
 void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out,
              void* pool_out, const float* head_w, const float* head_b, float* head_out, int B,
              int W, int H, int head_o, cudaStream_t st, const TcConfig* force = nullptr);
-std::vector<TcConfig> tc_candidates(const ConvLayer& L);
+std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision p);
+cudaError_t tc_prepare_fp8(ConvLayer& L);
 int tc_error_word();  // nonzero after a bounded wait in a tensor-core kernel ran out (then reset)
 
 }  // namespace lnr

@@ -8,8 +8,10 @@
 // GPU) and the layer orchestration shared by every precision.  Pooling, upsampling and
 // concatenation are fused into the convolutions: nothing but conv outputs is written.
 #include <cmath>
+#include <cuda_bf16.h>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "lnr_internal.h"
 
@@ -270,6 +272,62 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
     }
 }
 
+__global__ void k_amax_bf16(const __nv_bfloat16* __restrict__ x, size_t n, unsigned* __restrict__ out) {
+    float m = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as integers
+}
+
+// FP8 calibration, after a BF16 forward pass on ws: the largest magnitude of every
+// convolution's output gives that tensor's E4M3 scale (amax / 448); each layer's E4M3
+// weights then fold in the scales of its inputs.  The first conv keeps BF16 operands (its
+// input is the RGBDA image) and writes E4M3.
+lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
+    Unet& u = c->unet;
+    const void* in = ws.act[4 * kMaxUnetLevels].p;
+    const std::vector<ConvCall> calls = unet_plan(u, ws, LNR_BF16, in, ws.out.as<float>());
+    unsigned* d_amax = nullptr;
+    cudaError_t e = cudaMalloc(&d_amax, sizeof(unsigned) * calls.size());
+    if (e != cudaSuccess) return cuda_fail(c, e, "calibration");
+    cudaMemsetAsync(d_amax, 0, sizeof(unsigned) * calls.size(), ws.stream);
+    for (size_t i = 0; i < calls.size(); ++i) {
+        const ConvCall& k = calls[i];
+        if (k.head_out) continue;  // the last conv's features go straight into the head
+        const size_t n = (size_t)ws.B * k.W * k.H * u.convs[k.layer].cout;
+        k_amax_bf16<<<1024, 256, 0, ws.stream>>>(static_cast<const __nv_bfloat16*>(k.out), n, d_amax + i);
+    }
+    std::vector<unsigned> h(calls.size());
+    e = cudaMemcpyAsync(h.data(), d_amax, sizeof(unsigned) * calls.size(), cudaMemcpyDeviceToHost, ws.stream);
+    if (!e) e = cudaStreamSynchronize(ws.stream);
+    cudaFree(d_amax);
+    if (e != cudaSuccess) return cuda_fail(c, e, "calibration");
+    std::map<const void*, float> scale;  // activation tensor -> E4M3 scale
+    for (size_t i = 0; i < calls.size(); ++i) {
+        float a;
+        std::memcpy(&a, &h[i], 4);
+        const float sc = std::max(a, 1e-6f) / 448.0f;
+        u.convs[calls[i].layer].out_scale = sc;
+        scale[calls[i].out] = sc;
+        if (calls[i].pool) scale[calls[i].pool] = sc;  // a max-pool keeps the range
+    }
+    for (const ConvCall& k : calls) {
+        ConvLayer& L = u.convs[k.layer];
+        auto s0 = scale.find(k.src0);
+        if (s0 == scale.end()) {  // reads the BF16 input image
+            L.fp8 = false;
+            continue;
+        }
+        L.in_scale[0] = s0->second;
+        L.in_scale[1] = k.src1 ? scale.at(k.src1) : 1.f;
+        if ((e = tc_prepare_fp8(L)) != cudaSuccess) return cuda_fail(c, e, "FP8 weights");
+    }
+    u.fp8_ready = true;
+    c->unet_gen++;
+    return LNR_OK;
+}
+
 // Autotuner: for every tensor-core convolution of the forward pass at the workspace's
 // (B, W, H), time each candidate kernel configuration (CUDA events, `reps` launches after a
 // warm-up launch) on the layer's real buffers and keep the fastest for that layer
@@ -288,7 +346,7 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
         ConvLayer& L = u.convs[k.layer];
         float best = 1e30f;
         TcConfig best_cfg;
-        for (const TcConfig& cfg : tc_candidates(L)) {
+        for (const TcConfig& cfg : tc_candidates(L, p)) {
             run_call(u, k, ws, p, st, &cfg);  // warm-up (and first-use set-up)
             cudaEventRecord(e0, st);
             for (int r = 0; r < reps; ++r) run_call(u, k, ws, p, st, &cfg);
@@ -303,7 +361,7 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
             }
         }
         if (e != cudaSuccess) break;
-        L.tuned[{k.W, k.H}] = best_cfg;
+        (p == LNR_FP8 ? L.tuned8 : L.tuned)[{k.W, k.H}] = best_cfg;
         static const bool log = getenv("LNR_TUNE_LOG") != nullptr;
         if (log)
             fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d  %.1f us\n", k.layer, k.W, k.H, best_cfg.mode,
