@@ -173,6 +173,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_accuracy(args, scene, views, weights, lnr, synth):
+    """Max abs error and PSNR of each GPU precision against the oracle's FP64 U-Net (same
+    bit-exact U-Net input on both sides) on `args.accuracy` 1080p views."""
+    import oracle
+    intr = synth.intrinsics_for(W, H)
+    r = lnr.Renderer(0)
+    r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
+    r.build_grid(CELL)
+    r.set_unet(CH, weights, "bf16")
+    r.calibrate(views[0], intr, W, H, NLEV, FS[0])
+    g = oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
+    res = {p: {"max_abs": 0.0, "min_psnr": 1e9} for p in ("fp32", "bf16", "fp8")}
+    vs = synth.random_poses(scene, args.accuracy, seed=2)
+    for i, v in enumerate(vs):
+        fs = FS[i % 2]
+        ref = oracle.render(g, v, intr, W, H, NLEV, fs, weights, CH)["y"]
+        for p in ("fp32", "bf16", "fp8"):
+            r.set_precision(p)
+            y = r.render(v, intr, W, H, NLEV, fs)
+            d = np.abs(y.astype(np.float64) - ref)
+            mse = float(np.mean(d * d))
+            res[p]["max_abs"] = max(res[p]["max_abs"], float(d.max()))
+            res[p]["min_psnr"] = min(res[p]["min_psnr"], 10 * np.log10(1.0 / max(mse, 1e-30)))
+            res[p]["in_unit_range"] = bool(y.min() >= 0.0 and y.max() <= 1.0) and res[p].get("in_unit_range", True)
+    print(json.dumps({"accuracy": res, "views": args.accuracy, "workload": "multiroom_20M", "W": W, "H": H,
+                      "reference": "oracle FP64 U-Net on the bit-exact U-Net input"}), flush=True)
+    r.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +210,9 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy", type=int, default=0, metavar="VIEWS",
+                    help="report max abs error and PSNR of the FP32 / BF16 / FP8 U-Nets against the "
+                         "oracle's FP64 U-Net on VIEWS 1080p views (slow: the oracle runs on the host)")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched path only (no stage timing, plain, serving or CPU legs): "
                          "the command the ncu captures in profiles/ run")
@@ -203,6 +235,8 @@ def main():
     dev = torch.device("cuda", local)
 
     scene, views, weights = make_workload(dev)
+    if args.accuracy:
+        return run_accuracy(args, scene, views, weights, lnr, synth)
     stream = torch.cuda.Stream(device=dev)
     r = lnr.Renderer(local, stream=stream.cuda_stream)
     r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
@@ -308,6 +342,20 @@ def main():
     plain_ms, _ = timed(step_plain, max(3, args.steps // 2), 3)
     plain_fps = 1e3 / float(np.mean(plain_ms))
 
+    # ---- FP8 variant of the batched path (device-timed) ------------------------------
+    fp8 = None
+    if have_tc:
+        try:
+            r.calibrate(views[0], intr, W, H, NLEV, FS[0])
+            r.set_precision("fp8")
+            r.autotune(W, H, B)
+            fp8_ms, _ = timed(step, args.steps, args.warmup)
+            fp8 = {"value": B * args.steps / (float(np.sum(fp8_ms)) / 1e3), "unit": "frames/s",
+                   "calibration": "static per-tensor scales from one BF16 frame (pose 0)"}
+        except lnr.LnrError as e:
+            fp8 = {"unavailable": str(e)}
+        r.set_precision(prec)
+
     # ---- served paths through the public serving API (host result buffers) --------
     def serve_run(precision, max_batch, slots, n, lam, seed):
         """Submit n 1080p requests (all at once when lam is None, else Poisson arrivals at
@@ -382,6 +430,7 @@ def main():
                                           "arrivals_per_s": lam, "requests": int(n_open)}},
             "plain_fp32": {"value": plain_fps, "unit": "frames/s", "served_value": plain_srv_fps},
             "served_bf16": {"value": srv_fps, "unit": "frames/s"},
+            "batched_fp8": fp8,
             "stages_ms_per_batch": {k: round(float(np.median([t[k] for t in tims])), 4)
                                     for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]},
             "grid_build_ms": grid_ms,
