@@ -1292,7 +1292,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     HaloTypes ty;
     if (fp8) {
         ty.in8 = L.fp8;
-        ty.out8 = head_out == nullptr;
+        ty.out8 = head_out == nullptr && !L.out_bf16;
         ty.inv_out = 1.0f / L.out_scale;
         ty.cscale = L.fp8 ? L.wscale8 : nullptr;
     }

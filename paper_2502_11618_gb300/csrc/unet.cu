@@ -314,9 +314,18 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
     }
     for (const ConvCall& k : calls) {
         ConvLayer& L = u.convs[k.layer];
+        L.out_bf16 = false;
+    }
+    for (const ConvCall& k : calls) {
+        ConvLayer& L = u.convs[k.layer];
         auto s0 = scale.find(k.src0);
-        if (s0 == scale.end()) {  // reads the BF16 input image
+        if (s0 == scale.end() || k.head_out) {
+            // BF16 operands: the first conv (reads the BF16 input image) and the last one,
+            // whose features feed the output head directly; its producer then writes BF16
             L.fp8 = false;
+            if (k.head_out)
+                for (const ConvCall& q : calls)
+                    if (q.out == k.src0) u.convs[q.layer].out_bf16 = true;
             continue;
         }
         L.in_scale[0] = s0->second;

@@ -45,7 +45,7 @@ def test_fp8_needs_calibration(setup):
 
 def test_fp8_psnr_against_fp64(setup):
     lnr, s, g, ch, w, r = setup
-    W, H = 392, 264
+    W, H = 960, 544
     intr = synth.intrinsics_for(W, H)
     views = synth.random_poses(s, 4, seed=21)
     r.calibrate(views[0], intr, W, H, 4, 1.0)
