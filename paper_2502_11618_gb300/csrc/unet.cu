@@ -303,33 +303,35 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
     if (!e) e = cudaStreamSynchronize(ws.stream);
     cudaFree(d_amax);
     if (e != cudaSuccess) return cuda_fail(c, e, "calibration");
-    std::map<const void*, float> scale;  // activation tensor -> E4M3 scale
+    // Buffers are reused across levels (an encoder and a decoder conv of one level write
+    // the same slot), so the producer of an input is the LAST earlier call that wrote it.
+    std::vector<float> sc(calls.size());
     for (size_t i = 0; i < calls.size(); ++i) {
         float a;
         std::memcpy(&a, &h[i], 4);
-        const float sc = std::max(a, 1e-6f) / 448.0f;
-        u.convs[calls[i].layer].out_scale = sc;
-        scale[calls[i].out] = sc;
-        if (calls[i].pool) scale[calls[i].pool] = sc;  // a max-pool keeps the range
+        sc[i] = std::max(a, 1e-6f) / 448.0f;
+        u.convs[calls[i].layer].out_scale = sc[i];
+        u.convs[calls[i].layer].out_bf16 = false;
     }
-    for (const ConvCall& k : calls) {
+    auto producer = [&](size_t i, const void* buf) -> int {
+        for (size_t j = i; j-- > 0;)
+            if (calls[j].out == buf || (calls[j].pool && calls[j].pool == buf)) return (int)j;
+        return -1;  // the BF16 input image
+    };
+    for (size_t i = 0; i < calls.size(); ++i) {
+        const ConvCall& k = calls[i];
         ConvLayer& L = u.convs[k.layer];
-        L.out_bf16 = false;
-    }
-    for (const ConvCall& k : calls) {
-        ConvLayer& L = u.convs[k.layer];
-        auto s0 = scale.find(k.src0);
-        if (s0 == scale.end() || k.head_out) {
+        const int p0 = producer(i, k.src0);
+        if (p0 < 0 || k.head_out) {
             // BF16 operands: the first conv (reads the BF16 input image) and the last one,
             // whose features feed the output head directly; its producer then writes BF16
             L.fp8 = false;
-            if (k.head_out)
-                for (const ConvCall& q : calls)
-                    if (q.out == k.src0) u.convs[q.layer].out_bf16 = true;
+            if (k.head_out && p0 >= 0) u.convs[calls[p0].layer].out_bf16 = true;
             continue;
         }
-        L.in_scale[0] = s0->second;
-        L.in_scale[1] = k.src1 ? scale.at(k.src1) : 1.f;
+        L.in_scale[0] = sc[p0];
+        const int p1 = k.src1 ? producer(i, k.src1) : -1;
+        L.in_scale[1] = p1 >= 0 ? sc[p1] : 1.f;
         if ((e = tc_prepare_fp8(L)) != cudaSuccess) return cuda_fail(c, e, "FP8 weights");
     }
     u.fp8_ready = true;
