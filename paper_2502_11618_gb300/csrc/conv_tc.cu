@@ -446,7 +446,7 @@ struct HParams {
     const float* cscale;        // per-output-channel accumulator scale (FP8 operands), or null
     void* out;                  // NHWC output, BF16 or (out_fp8) E4M3
     void* pool_out;             // 2x2 max-pooled output, same type, or null
-    int out_fp8;
+    int out_fp8, pool_fp8;      // output / pooled output stored as E4M3 (else BF16)
     float inv_out;              // E4M3 output: value * inv_out is stored
     const float* head_w;
     const float* head_b;
@@ -756,11 +756,13 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         if (p.out_fp8) {
                             if (v0) st_fp8x16(static_cast<uint8_t*>(p.out) + e0, f0, p.inv_out);
                             if (v1) st_fp8x16(static_cast<uint8_t*>(p.out) + e1, f1, p.inv_out);
-                            if ((m & 1) == 0 && v1) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + ep, pm, p.inv_out);
                         } else {
                             if (v0) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e0, f0);
                             if (v1) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e1, f1);
-                            if ((m & 1) == 0 && v1) st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
+                        }
+                        if ((m & 1) == 0 && v1) {
+                            if (p.pool_fp8) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + ep, pm, p.inv_out);
+                            else st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
                         }
                     }
                 }
@@ -1130,7 +1132,7 @@ void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
 
 // Element encoding of one halo-kernel launch: BF16 or E4M3 operands, BF16 or E4M3 output.
 struct HaloTypes {
-    bool in8 = false, out8 = false;
+    bool in8 = false, out8 = false, pool8 = false;
     float inv_out = 1.f;
     const float* cscale = nullptr;
 };
@@ -1234,6 +1236,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.out = out;
     p.pool_out = pool_out;
     p.out_fp8 = ty.out8;
+    p.pool_fp8 = ty.pool8;
     p.inv_out = ty.inv_out;
     p.head_w = head_w;
     p.head_b = head_b;
@@ -1293,6 +1296,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     if (fp8) {
         ty.in8 = L.fp8;
         ty.out8 = head_out == nullptr && !L.out_bf16;
+        ty.pool8 = !L.pool_bf16;
         ty.inv_out = 1.0f / L.out_scale;
         ty.cscale = L.fp8 ? L.wscale8 : nullptr;
     }

@@ -61,7 +61,8 @@ struct ConvLayer {
     // first, whose input is the BF16 RGBDA image); in_scale: activation scale of each K
     // segment's input; out_scale: of this conv's output; wscale8: per output channel.
     bool fp8 = false;
-    bool out_bf16 = false;  // FP8 mode: this conv's consumer reads BF16 (the head conv)
+    bool out_bf16 = false;  // FP8 mode: a consumer of this conv's output reads BF16 operands
+    bool pool_bf16 = false; // FP8 mode: the consumer of its pooled output reads BF16
     float in_scale[2] = {1.f, 1.f};
     float out_scale = 1.f;
     void* wh8[3] = {nullptr, nullptr, nullptr};

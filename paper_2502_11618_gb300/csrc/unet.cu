@@ -318,21 +318,36 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
             if (calls[j].out == buf || (calls[j].pool && calls[j].pool == buf)) return (int)j;
         return -1;  // the BF16 input image
     };
+    // BF16 operands for the first conv (the BF16 input image) and for the full-resolution
+    // decoder level (its two convs feed the output head; E4M3 there costs the most
+    // accuracy); E4M3 everywhere else.  A producer writes BF16 for a BF16 consumer.
+    const int nenc = 2 * u.levels;
     for (size_t i = 0; i < calls.size(); ++i) {
         const ConvCall& k = calls[i];
         ConvLayer& L = u.convs[k.layer];
+        L.pool_bf16 = false;
         const int p0 = producer(i, k.src0);
-        if (p0 < 0 || k.head_out) {
-            // BF16 operands: the first conv (reads the BF16 input image) and the last one,
-            // whose features feed the output head directly; its producer then writes BF16
-            L.fp8 = false;
-            if (k.head_out && p0 >= 0) u.convs[calls[p0].layer].out_bf16 = true;
-            continue;
+        const bool bf16 = p0 < 0 || (k.layer >= nenc && L.level == 0);
+        L.fp8 = !bf16;
+        if (bf16) {
+            for (const void* src : {k.src0, k.src1}) {
+                if (!src) continue;
+                const int pj = producer(i, src);
+                if (pj < 0) continue;
+                if (calls[pj].out == src) u.convs[calls[pj].layer].out_bf16 = true;
+                else u.convs[calls[pj].layer].pool_bf16 = true;
+            }
         }
-        L.in_scale[0] = sc[p0];
+    }
+    for (size_t i = 0; i < calls.size(); ++i) {
+        const ConvCall& k = calls[i];
+        ConvLayer& L = u.convs[k.layer];
+        if (!L.fp8) continue;
+        L.in_scale[0] = sc[producer(i, k.src0)];
         const int p1 = k.src1 ? producer(i, k.src1) : -1;
         L.in_scale[1] = p1 >= 0 ? sc[p1] : 1.f;
         if ((e = tc_prepare_fp8(L)) != cudaSuccess) return cuda_fail(c, e, "FP8 weights");
+        L.fp8 = true;
     }
     u.fp8_ready = true;
     c->unet_gen++;
