@@ -138,7 +138,7 @@ lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
 
 /* Calibrate the FP8 (E4M3) U-Net on one view (after set_unet): the view is rendered with
  * the BF16 U-Net, the largest magnitude of every convolution's output sets that tensor's
- * static scale (amax / 448), and E4M3 weights with per-output-channel scales are built
+ * static scale (8 x amax / 448: headroom for views with larger activations), and E4M3 weights with per-output-channel scales are built
  * with the input scales folded in; accumulation stays FP32 (the paper states no precision;
  * SURVEY precision pattern).  Afterwards lnr_set_precision(LNR_FP8) is allowed.  Arguments
  * as lnr_render.  Errors: as lnr_render; LNR_E_ARG when a channel count of the net is not a
