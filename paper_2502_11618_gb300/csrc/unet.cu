@@ -273,6 +273,7 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
 }
 
 constexpr float kFp8Headroom = 8.0f;
+constexpr bool kFp8Level0DecoderBf16 = false;
 
 __global__ void k_amax_bf16(const __nv_bfloat16* __restrict__ x, size_t n, unsigned* __restrict__ out) {
     float m = 0.f;
@@ -323,16 +324,16 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
             if (calls[j].out == buf || (calls[j].pool && calls[j].pool == buf)) return (int)j;
         return -1;  // the BF16 input image
     };
-    // BF16 operands for the first conv (the BF16 input image) and for the full-resolution
-    // decoder level (its two convs feed the output head; E4M3 there costs the most
-    // accuracy); E4M3 everywhere else.  A producer writes BF16 for a BF16 consumer.
+    // BF16 operands for the first conv (the BF16 input image) and the last one (its
+    // features feed the output head directly) -- optionally the whole full-resolution
+    // decoder level; E4M3 everywhere else.  A producer writes BF16 for a BF16 consumer.
     const int nenc = 2 * u.levels;
     for (size_t i = 0; i < calls.size(); ++i) {
         const ConvCall& k = calls[i];
         ConvLayer& L = u.convs[k.layer];
         L.pool_bf16 = false;
         const int p0 = producer(i, k.src0);
-        const bool bf16 = p0 < 0 || (k.layer >= nenc && L.level == 0);
+        const bool bf16 = p0 < 0 || k.head_out || (kFp8Level0DecoderBf16 && k.layer >= nenc && L.level == 0);
         L.fp8 = !bf16;
         if (bf16) {
             for (const void* src : {k.src0, k.src1}) {
