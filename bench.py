@@ -105,6 +105,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_pose(i, rank, n_poses=N_POSES):
+    """Pose index of view i on replica `rank`: every rank renders its own poses."""
+    return (i * 7 + rank * 3) % n_poses
+
+
+def aggregate(tot_ms, frames_per_rank, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the frames of all ranks divided by the
+    slowest rank's time (max over ranks)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    return frames_per_rank * world / (tot_ms / 1e3), tot_ms
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -257,7 +275,7 @@ def main():
     r.autotune(W, H, B)          # per-layer conv kernel choice (outside every timed region)
     tune_s = time.perf_counter() - t0
     # every rank renders its own poses (replicas: views are independent)
-    pose = lambda i: views[(i * 7 + rank * 3) % len(views)]
+    pose = lambda i: views[replica_pose(i, rank, len(views))]
     out = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
 
     def step(i):
@@ -272,6 +290,7 @@ def main():
         if world > 1:
             dist.barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.nvtx.range_push("timed")     # ncu captures select launches inside this range
         t0 = time.perf_counter()
         for i in range(K):
             with torch.cuda.stream(stream):
@@ -281,6 +300,7 @@ def main():
                 evs[i][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         if world > 1:
             dist.barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
@@ -290,13 +310,7 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     step_ms, wall = timed(step, args.steps, args.warmup)
-    tot_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    frames = B * args.steps * world
-    value = frames / (tot_ms / 1e3)
+    value, tot_ms = aggregate(float(np.sum(step_ms)), B * args.steps, dist if world > 1 else None, dev)
 
     if args.only_batched:
         clocks.stop()
