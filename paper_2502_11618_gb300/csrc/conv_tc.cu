@@ -422,8 +422,11 @@ constexpr int kHaloW = 130;  // staged pixels per halo row
 
 struct HSeg {
     CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {ck, 130, rows, 1}; kind 1: 5-D, box {ck, 1, 130, rows, 1}
-    CUtensorMap b;   // 3-D {ck, N, 9 * chunks}, box {ck, N, 9}: weights [chunk][tap][N][ck]
+    CUtensorMap b;   // 3-D {ck, N, wblk * chunks}, box {ck, N, bload}: weights [chunk][block][N][ck]
     int kind;        // 0: same-resolution source; 1: skip (parity tiles); 2: coarse (parity tiles)
+    int wblk;        // weight blocks per chunk in memory (9, or 16 for the coarse operand)
+    int bload;       // blocks staged per chunk (9; coarse: 16 for 4 classes, else the tile's y class's 8)
+    int bsel;        // 1: the staged blocks start at 8 * (tile's y class)
     int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel
     int rows;        // halo rows staged
     int nchunk;      // K chunks of this segment
@@ -601,7 +604,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     } else {
                         tma_4d(a_dst, &s.a, full(st), c, x0 - 1, y0 - 1, n);
                     }
-                    tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, cc * 9);
+                    tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, cc * s.wblk + (s.bsel ? 8 * py : 0));
                     ++use;
                 }
             }
@@ -610,12 +613,15 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
     } else if (warp >= 1 && warp <= kMmaWarps && lane == 0 && warp - 1 < p.nmma) {
         // ----------------------------------------------------------------- MMA --
-        // Issuer g owns accumulators [a_lo, a_hi] of every tile (a = class * R + row).
-        // Descriptors are built once per stage; every tap, row and K step only adds a
-        // constant to the start-address field (address >> 4, 14 bits).
-        constexpr int NCA = PAR == 0 ? 1 : PAR;
-        const int g = warp - 1, nacc = NCA * R;
-        const int a_lo = g * nacc / p.nmma, a_hi = (g + 1) * nacc / p.nmma - 1;
+        // Issuer g owns work units [a_lo, a_hi] of every tile: standard tiles one output row
+        // each; parity tiles one (row, y class) each, owning the accumulators of its NX x
+        // classes (adjacent in TMEM, cx = 1 first).  Descriptors are built once per stage;
+        // every tap, row and K step only adds a constant to the start-address field
+        // (address >> 4, 14 bits).
+        constexpr int NY = PAR == 4 ? 2 : 1, NX = PAR >= 2 ? 2 : 1;
+        const int g = warp - 1, nunit = NY * R;
+        const int a_lo = g * nunit / p.nmma, a_hi = (g + 1) * nunit / p.nmma - 1;
+        const uint32_t idesc2 = (p.idesc & ~(0x3Fu << 17)) | ((uint32_t)(2 * N >> 3) << 17);
         int use = 0, tcount = 0;
         bool ok = true, issued = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
@@ -626,7 +632,6 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
             tc_fence_after();
             constexpr int NACC = R * (PAR == 0 ? 1 : PAR);
             const uint32_t d0 = tmem + (uint32_t)(b * NACC * N);
-            uint32_t first = 1;
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
                 const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16;
@@ -671,32 +676,59 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                     }
                                 }
                             }
-                    } else {
-                        // decoder concat conv: accumulator a = class * R + row; the A tile of
-                        // (class, tap) is a shifted row of the staged skip planes or coarse rows
-                        for (int tap = 0; tap < 9; ++tap) {
-                            const int ky = tap / 3, kx = tap - 3 * ky;
-                            for (int k = 0; k < nk; ++k) {
-                                const uint64_t bd = hi | (uint64_t)(b0 + tap * btap + 2 * k);
-                                const uint32_t acc = (cc | tap | k) ? 1u : 0u;
-                                for (int a = a_lo; a <= a_hi; ++a) {
-                                    const int c = a / R, r = a - c * R;
-                                    const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
-                                    const int cpy = PAR == 4 ? (c >> 1) : py;
-                                    uint32_t off;
-                                    if (skip) {
-                                        const int dxf = cpx + kx - 1;
-                                        off = (uint32_t)(dxf & 1) * plane16 + (uint32_t)((PAR == 4 ? cpy : 0) + ky + 2 * r) * row16 +
-                                              (uint32_t)(1 + (dxf >> 1)) * pitch16;
+                    } else if (skip) {
+                        // decoder concat conv, skip operand: the fine pixel of class cx at tap
+                        // (ky, kx) is x-offset dxf = cx + kx - 1 from 2X, i.e. plane dxf & 1,
+                        // staged column 1 + (dxf >> 1).  With both x classes in the tile, the
+                        // offsets dxf = 0 and 1 serve both classes with weight blocks (ky, dxf)
+                        // and (ky, dxf + 1), adjacent in shared memory, into the unit's two
+                        // adjacent accumulators [cx = 1, cx = 0]: one MMA of 2N columns.
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int k = 0; k < nk; ++k)
+                                for (int u = a_lo; u <= a_hi; ++u) {
+                                    const int r = u / NY, cy = PAR == 4 ? u - r * NY : py;
+                                    const uint32_t du = d0 + (uint32_t)(u * NX * N);
+                                    const uint32_t ar = a0 + (uint32_t)((PAR == 4 ? cy : 0) + ky + 2 * r) * row16 + 2 * k;
+                                    auto A = [&](int dxf) {
+                                        return hi | (uint64_t)(ar + (uint32_t)(dxf & 1) * plane16 + (uint32_t)(1 + (dxf >> 1)) * pitch16);
+                                    };
+                                    const uint32_t bk = b0 + (uint32_t)(3 * ky) * btap + 2 * k;
+                                    if (NX == 2) {
+                                        mma_op<IN8>(du, A(0), hi | (uint64_t)bk, idesc2, (cc | ky | k) ? 1u : 0u);
+                                        mma_op<IN8>(du, A(1), hi | (uint64_t)(bk + btap), idesc2, 1u);
+                                        mma_op<IN8>(du + (uint32_t)N, A(-1), hi | (uint64_t)bk, p.idesc, 1u);
+                                        mma_op<IN8>(du, A(2), hi | (uint64_t)(bk + 2 * btap), p.idesc, 1u);
                                     } else {
-                                        off = (uint32_t)(1 + r + ((cpy + ky - 1) >> 1)) * row16 +
-                                              (uint32_t)(1 + ((cpx + kx - 1) >> 1)) * pitch16;
+                                        for (int kx = 0; kx < 3; ++kx)
+                                            mma_op<IN8>(du, A(px + kx - 1), hi | (uint64_t)(bk + kx * btap), p.idesc,
+                                                        (cc | ky | k | kx) ? 1u : 0u);
                                     }
-                                    mma_op<IN8>(d0 + (uint32_t)(a * N), hi | (uint64_t)(a0 + off + 2 * k), bd, p.idesc,
-                                             (sg == 0) ? acc : 1u);
                                 }
-                            }
-                        }
+                    } else {
+                        // decoder concat conv, nearest-upsampled operand: class (cx, cy) reads
+                        // coarse rows cy - 1 + j (j = 0, 1) and columns dxc in {cx - 1, cx},
+                        // each with the sum of the 3x3 taps that land on that coarse pixel
+                        // (blocks per (cy, j): [cx=1 dxc=+1][cx=1 dxc=0][cx=0 dxc=0][cx=0 dxc=-1]);
+                        // dxc = 0 serves both x classes with one MMA of 2N columns.
+                        for (int j = 0; j < 2; ++j)
+                            for (int k = 0; k < nk; ++k)
+                                for (int u = a_lo; u <= a_hi; ++u) {
+                                    const int r = u / NY, cy = PAR == 4 ? u - r * NY : py;
+                                    const uint32_t du = d0 + (uint32_t)(u * NX * N);
+                                    const uint32_t ar = a0 + (uint32_t)(1 + r + cy - 1 + j) * row16 + 2 * k;
+                                    const uint32_t bj = b0 + (uint32_t)((PAR == 4 ? 8 * cy : 0) + 4 * j) * btap + 2 * k;
+                                    if (NX == 2) {
+                                        mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, p.idesc, 1u);
+                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), idesc2, 1u);
+                                        mma_op<IN8>(du + (uint32_t)N, hi | (uint64_t)ar, hi | (uint64_t)(bj + 3 * btap), p.idesc, 1u);
+                                    } else if (px == 1) {
+                                        mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, p.idesc, 1u);
+                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), p.idesc, 1u);
+                                    } else {
+                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + 2 * btap), p.idesc, 1u);
+                                        mma_op<IN8>(du, hi | (uint64_t)ar, hi | (uint64_t)(bj + 3 * btap), p.idesc, 1u);
+                                    }
+                                }
                     }
                     issued = true;
                     mma_commit(empty(st));
@@ -768,18 +800,20 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                 }
             } else {
                 for (int a = 0; a < NCE * R; ++a) {
-                    const int c = a / R, r = a % R;
                     int x, y;
                     bool v;
                     if (PAR) {
-                        const int cpx = PAR == 4 ? (c & 1) : PAR == 2 ? c : px;
-                        const int cpy = PAR == 4 ? (c >> 1) : py;
+                        // accumulator a: unit a / NX = (row, y class), x class 1 before 0
+                        constexpr int NYE = PAR == 4 ? 2 : 1, NXE = PAR >= 2 ? 2 : 1;
+                        const int u = a / NXE, r = u / NYE;
+                        const int cpx = NXE == 2 ? 1 - (a & 1) : px;
+                        const int cpy = PAR == 4 ? u - r * NYE : py;
                         x = 2 * (x0 + m) + cpx;
                         y = 2 * (y0 + r) + cpy;
                         v = (x0 + m) < Wh && (y0 + r) < Hh;
                     } else {
                         x = x0 + m;
-                        y = y0 + r;
+                        y = y0 + a;
                         v = x < p.W && y < p.H;
                     }
                     const size_t pix = ((size_t)n * p.H + y) * p.W + x;
@@ -799,7 +833,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                         : 0.f;
                         }
                         if (p.head_out) {
-                            for (int o = 0; o < p.head_o; ++o) {
+#pragma unroll
+                            for (int o = 0; o < 4; ++o) {  // head_o <= 4: h stays in registers
+                                if (o >= p.head_o) break;
                                 float sacc = 0.f;
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
@@ -818,9 +854,13 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                             }
                         }
                     }
-                    if (p.head_out && v)
-                        for (int o = 0; o < p.head_o; ++o)
+                    if (p.head_out && v) {
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            if (o >= p.head_o) break;
                             p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[p.head_o * N + o])));
+                        }
+                    }
                 }
             }
             tc_fence_before();
@@ -1015,12 +1055,50 @@ static uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 
 
+// Weight blocks of one K chunk of segment sg of the halo kernel, as 9-bit tap masks (bit
+// 3 * ky + kx); a block holds the sum of its taps' weights.
+//  - standard convs: single taps ordered [kx][ky = 2, 1, 0], so that the blocks of one kx
+//    and consecutive output rows form one contiguous B operand;
+//  - decoder concat convs, skip operand: single taps [ky][kx];
+//  - decoder concat convs, nearest-upsampled operand: for output class (cx, cy) the 3x3
+//    taps fall on only 2 x 2 coarse pixels (coarse offset ((c + k - 1) >> 1) per axis), so
+//    the conv of the upsampled tensor is a 2x2 conv of the coarse one with summed taps.
+//    Blocks per (cy, j = coarse row cy - 1 + j): [cx=1 dxc=+1][cx=1 dxc=0][cx=0 dxc=0]
+//    [cx=0 dxc=-1], 16 per chunk.
+static std::vector<uint16_t> halo_blocks(const ConvLayer& L, int sg) {
+    std::vector<uint16_t> b;
+    if (!L.cin1) {
+        for (int j = 0; j < 9; ++j) b.push_back((uint16_t)(1u << ((2 - j % 3) * 3 + j / 3)));
+    } else if (sg == 0) {
+        for (int t = 0; t < 9; ++t) b.push_back((uint16_t)(1u << t));
+    } else {
+        const int cls[4][2] = {{1, 1}, {1, 0}, {0, 0}, {0, -1}};  // (cx, dxc)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int j = 0; j < 2; ++j)
+                for (const auto& c : cls) {
+                    uint16_t m = 0;
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx)
+                            if (((cy + ky - 1) >> 1) == cy - 1 + j && ((c[0] + kx - 1) >> 1) == c[1])
+                                m |= (uint16_t)(1u << (3 * ky + kx));
+                    b.push_back(m);
+                }
+    }
+    return b;
+}
+
+// Original input channel of padded channel ch of a layer (-1 for the RGBDA padding).
+static int halo_src(const ConvLayer& L, int ch) {
+    const int c0 = tc_c0(L);
+    if (ch < c0) return ch < L.cin0 ? ch : -1;
+    return L.cin0 + (ch - c0);
+}
+
 // Weights of the halo kernel for chunks of at most ckmax channels: every K segment's
-// chunks in turn, each chunk [tap][N][ck] with ck = seg_ck(C_segment, ckmax) -- one TMA box
-// {ck, N, 9} per chunk, swizzled like the halo rows.  Standard convs store their tap blocks
-// as [kx][ky = 2, 1, 0] (the blocks of one kx and consecutive output rows then form one
-// contiguous B operand); decoder concat convs as [ky][kx].  value(n, src, t) gives the
-// weight of output n, original input channel src, tap t; enc(v) its stored bytes.
+// chunks in turn, each chunk [block][N][ck] with ck = seg_ck(C_segment, ckmax) -- one TMA
+// box {ck, N, blocks} per chunk, swizzled like the halo rows.  value(n, src, mask) gives
+// the (summed) weight of output n, original input channel src over the taps in mask;
+// enc(v) its stored bytes.
 template <class T, class Value, class Enc>
 static cudaError_t halo_weights(const ConvLayer& L, int ckmax, Value value, Enc enc, void*& dst) {
     const int c0 = tc_c0(L), N = L.cout;
@@ -1029,18 +1107,14 @@ static cudaError_t halo_weights(const ConvLayer& L, int ckmax, Value value, Enc 
     std::vector<T> w;
     for (int sg = 0; sg < nseg; ++sg) {
         const int ck = seg_ck(segC[sg], ckmax);
+        const std::vector<uint16_t> blk = halo_blocks(L, sg);
         for (int cc = 0; cc < segC[sg] / ck; ++cc)
-            for (int j = 0; j < 9; ++j) {
-                const int t = L.cin1 ? j : (2 - j % 3) * 3 + j / 3;
+            for (uint16_t m : blk)
                 for (int n = 0; n < N; ++n)
                     for (int e = 0; e < ck; ++e) {
-                        const int ch = segOff[sg] + cc * ck + e;  // padded channel
-                        int src;
-                        if (ch < c0) src = ch < L.cin0 ? ch : -1;
-                        else src = L.cin0 + (ch - c0);
-                        w.push_back(enc(src >= 0 ? value(n, src, t) : 0.f));
+                        const int src = halo_src(L, segOff[sg] + cc * ck + e);
+                        w.push_back(enc(src >= 0 ? value(n, src, m) : 0.f));
                     }
-            }
     }
     if (dst) cudaFree(dst);
     dst = nullptr;
@@ -1049,32 +1123,49 @@ static cudaError_t halo_weights(const ConvLayer& L, int ckmax, Value value, Enc 
     return cudaMemcpy(dst, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Sum of f(t) over the taps t in mask, in double, rounded once to float.
+template <class F>
+static float tap_sum(uint16_t mask, F f) {
+    double acc = 0.0;
+    for (int t = 0; t < 9; ++t)
+        if (mask >> t & 1) acc += (double)f(t);
+    return (float)acc;
+}
+
 static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax) {
     const int cin = L.cin0 + L.cin1;
     return halo_weights<__nv_bfloat16>(
-        L, ckmax, [&](int n, int src, int t) { return L.wf[((size_t)n * cin + src) * 9 + t]; },
+        L, ckmax,
+        [&](int n, int src, uint16_t m) { return tap_sum(m, [&](int t) { return L.wf[((size_t)n * cin + src) * 9 + t]; }); },
         [](float v) { return __float2bfloat16(v); }, L.wh[ck_index(ckmax)]);
 }
 
 // E4M3 weights of an FP8 layer: w * (scale of the input segment the channel comes from),
-// divided by a per-output-channel scale so that each channel's largest |w| maps to 448.
+// divided by a per-output-channel scale so that each channel's largest stored |w| (after
+// tap sums) maps to 448.
 cudaError_t tc_prepare_fp8(ConvLayer& L) {
-    const int cin = L.cin0 + L.cin1, N = L.cout;
+    const int cin = L.cin0 + L.cin1, N = L.cout, c0 = tc_c0(L);
     std::vector<float> sw(N, 0.f);
-    auto scaled = [&](int n, int src, int t) {
-        return L.wf[((size_t)n * cin + src) * 9 + t] * (src < L.cin0 ? L.in_scale[0] : L.in_scale[1]);
+    auto scaled = [&](int n, int src, uint16_t m) {
+        const float sc = src < L.cin0 ? L.in_scale[0] : L.in_scale[1];
+        return tap_sum(m, [&](int t) { return L.wf[((size_t)n * cin + src) * 9 + t]; }) * sc;
     };
+    const int segC[2] = {c0, L.cin1}, segOff[2] = {0, c0};
     for (int n = 0; n < N; ++n) {
-        float m = 0.f;
-        for (int src = 0; src < cin; ++src)
-            for (int t = 0; t < 9; ++t) m = std::max(m, std::fabs(scaled(n, src, t)));
-        sw[n] = std::max(m, 1e-30f) / 448.0f;
+        float mx = 0.f;
+        for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg)
+            for (uint16_t m : halo_blocks(L, sg))
+                for (int ch = segOff[sg]; ch < segOff[sg] + segC[sg]; ++ch) {
+                    const int src = halo_src(L, ch);
+                    if (src >= 0) mx = std::max(mx, std::fabs(scaled(n, src, m)));
+                }
+        sw[n] = std::max(mx, 1e-30f) / 448.0f;
     }
     cudaError_t e;
     for (int i = 0; i < 3; ++i) {
         const int ck = 32 << i;
         e = halo_weights<__nv_fp8_storage_t>(
-            L, ck, [&](int n, int src, int t) { return scaled(n, src, t) / sw[n]; },
+            L, ck, [&](int n, int src, uint16_t m) { return scaled(n, src, m) / sw[n]; },
             [](float v) { return __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }, L.wh8[i]);
         if (e != cudaSuccess) return e;
     }
@@ -1084,6 +1175,13 @@ cudaError_t tc_prepare_fp8(ConvLayer& L) {
     L.fp8 = true;
     return cudaMemcpy(L.wscale8, sw.data(), 4 * N, cudaMemcpyHostToDevice);
 }
+
+// Weight blocks staged per chunk: 9, or for the nearest-upsampled operand of a decoder
+// concat conv 16 (all four classes) or the 8 of the tile's y class.
+static int halo_bload(int kind, int P) { return kind == 2 ? (P == 4 ? 16 : 8) : 9; }
+
+// Parity-class tiles stack the two x classes along N (MMAs of 2N columns, at most 256).
+static bool halo_parity_ok(const ConvLayer& L, int P) { return P == 1 || (P >= 2 && 2 * L.cout <= 256); }
 
 // Bytes of one pipeline stage of the halo kernel for a layer at tile height R, P parity
 // classes per tile (decoder concat convs) and chunks of at most ckmax channels.
@@ -1095,7 +1193,8 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const int kind1 = L.cin1 && sg == 0;
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
-        st = std::max(st, align_up((kind1 ? 2 : 1) * plane + 9u * L.cout * pitch, 1024));
+        const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
+        st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)halo_bload(kind, P) * L.cout * pitch, 1024));
     }
     return st;
 }
@@ -1113,7 +1212,7 @@ void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
                 const int pp = L.cin1 ? Ps[pi] : 1;
                 if (area % pp) continue;
                 const int r = area / pp;
-                if (2 * area * N > 512 || (L.pool && (r & 1))) continue;
+                if (2 * area * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, pp))) continue;
                 const int cks[2] = {64, 32};
                 for (int i = 0; i < (pass ? 1 : 2); ++i) {
                     const int ck = pass ? 16 : cks[i];
@@ -1149,15 +1248,15 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     std::memset(&p, 0, sizeof(p));
     const int N = L.cout, c0 = tc_c0(L);
     if (!L.cin1) P = 0;
-    else if (P != 1 && P != 2 && P != 4) return false;
+    else if ((P != 1 && P != 2 && P != 4) || !halo_parity_ok(L, P)) return false;
     const int NC = P ? P : 1;
     if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * NC * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = P;
     p.wmax = std::max(1, std::min(3, 256 / N));
-    // two issuers for standard tiles (each takes half the rows and windows within it), one
-    // per accumulator (up to four) for the parity classes of the decoder concat convs
-    p.nmma = P ? std::min(kMmaWarps, NC * R) : (R >= 2 ? 2 : 1);
+    // two issuers for standard tiles (each takes half the rows and windows within it); for
+    // the decoder concat convs one per (row, y class) unit, up to four
+    p.nmma = P ? std::min(kMmaWarps, (P == 4 ? 2 : 1) * R) : (R >= 2 ? 2 : 1);
     const cuuint64_t eb = (cuuint64_t)esize;
     const CUtensorMapDataType dt = ty.in8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     size_t w_off = 0;  // bytes into wh
@@ -1173,7 +1272,10 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.plane = align_up((uint32_t)s.rows * kHaloW * s.pitch, 1024);
         s.a_bytes = planes * (uint32_t)s.rows * kHaloW * s.pitch;
         s.b_off = planes * s.plane;
-        const uint32_t b_bytes = 9u * N * s.pitch;
+        s.wblk = kind == 2 ? 16 : 9;
+        s.bload = halo_bload(kind, P);
+        s.bsel = kind == 2 && P != 4;
+        const uint32_t b_bytes = (uint32_t)s.bload * N * s.pitch;
         s.bytes = s.a_bytes + b_bytes;
         stage = std::max(stage, align_up(s.b_off + b_bytes, 1024));
         cuuint32_t es[5] = {1, 1, 1, 1, 1};
@@ -1193,13 +1295,13 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                               swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
-        cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)9 * s.nchunk};
+        cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)s.wblk * s.nchunk};
         cuuint64_t wstr[2] = {s.ck * eb, (cuuint64_t)N * s.ck * eb};
-        cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, 9};
+        cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, (cuuint32_t)s.bload};
         ok = ok && encode_tiled(&s.b, dt, 3, const_cast<uint8_t*>(wh + w_off), wd, wstr, wbox, es,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        w_off += (size_t)s.nchunk * 9 * N * s.ck * esize;
+        w_off += (size_t)s.nchunk * s.wblk * N * s.ck * esize;
         return ok;
     };
     bool ok;
@@ -1343,7 +1445,7 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
     for (int r : {1, 2, 4, 8})
         for (int pi = 0; pi < (L.cin1 ? 3 : 1); ++pi) {
             const int P = L.cin1 ? Ps[pi] : 0, NC = P ? P : 1;
-            if (2 * NC * r * N > 512 || (L.pool && (r & 1))) continue;
+            if (2 * NC * r * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, P))) continue;
             int last_ck[2] = {-1, -1};
             for (int ck : {16, 32, 64, 128}) {
                 if (ck * esize > 128 || (in8 && ck < 32)) continue;
