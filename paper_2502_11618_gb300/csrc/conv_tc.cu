@@ -510,6 +510,149 @@ __device__ __forceinline__ uint64_t sdesc_hi(uint32_t sbo, uint32_t swz) {
     return ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swz << 61);
 }
 
+// ---- MMA issue of one pipeline stage, fully unrolled ----
+//
+// One thread issues about one tcgen05.mma per 50-110 cycles; loop control and descriptor
+// arithmetic with run-time bounds made that several times slower.  The issue sequence of a
+// stage is therefore unrolled at compile time over taps, K steps (NK MMAs of 32 bytes of
+// K) and the issuer's rows / units, so that every descriptor is a per-stage base plus a
+// constant.
+
+// Work split of a tile among its MMA-issuing threads: standard tiles give each of
+// issuers(R) threads RPI consecutive output rows; parity tiles give each of up to four
+// threads UPI (row, y class) units.
+template <int R, int PAR>
+struct IssueSplit {
+    static constexpr int NY = PAR == 4 ? 2 : 1;
+    static constexpr int units = PAR == 0 ? R : NY * R;
+    static constexpr int issuers = PAR == 0 ? (R >= 2 ? 2 : 1) : (units < kMmaWarps ? units : kMmaWarps);
+    static constexpr int per = units / issuers;
+};
+
+struct IssueCtx {
+    int g;           // issuer index
+    int px, py;      // parity class of the tile (PAR 1 and 2)
+    uint32_t N;      // output channels
+    uint32_t idesc;  // instruction descriptor for N columns
+};
+
+__device__ __forceinline__ uint32_t idesc_n(uint32_t idesc, uint32_t n) {
+    return (idesc & ~(0x3Fu << 17)) | ((n >> 3) << 17);
+}
+
+template <int R, int PAR, bool IN8, int NK>
+__device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t a0, uint32_t b0, const HSeg& s, uint32_t d0,
+                                            bool first) {
+    using Sp = IssueSplit<R, PAR>;
+    constexpr int PER = Sp::per;
+    const uint32_t N = q.N;
+    const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16, btap = N * pitch16;
+    const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
+    if (PAR == 0) {
+        // Halo row h shifted by kx feeds output rows r = h - ky, ky = 0..2; the rows of one
+        // halo row go into one MMA (accumulators adjacent in TMEM, weight blocks [kx][ky =
+        // 2,1,0] adjacent in shared memory, N = rows * Cout <= 256).  In the stage's first
+        // (kx, k) step every row is first touched alone (h = r), zeroing it on a tile's
+        // first chunk, and the rest of that step covers h - r = 1, 2.
+        const uint32_t d = d0 + (uint32_t)(q.g * PER) * N;
+        const uint32_t a = a0 + (uint32_t)(q.g * PER) * row16;
+        const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const uint32_t ak = a + (uint32_t)kx * pitch16 + 2 * k, bk = b0 + 2 * k;
+                if (kx == 0 && k == 0) {
+#pragma unroll
+                    for (int r = 0; r < PER; ++r)
+                        mma_op<IN8>(d + (uint32_t)r * N, hi | (uint64_t)(ak + (uint32_t)r * row16), hi | (uint64_t)(bk + 2 * btap),
+                                    q.idesc, acc0);
+#pragma unroll
+                    for (int h = 1; h < PER + 2; ++h) {
+                        const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h - 1 < PER - 1 ? h - 1 : PER - 1;
+                        const int blk = 2 - (h - rlo);
+                        mma_op<IN8>(d + (uint32_t)rlo * N, hi | (uint64_t)(ak + (uint32_t)h * row16),
+                                    hi | (uint64_t)(bk + (uint32_t)blk * btap), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < PER + 2; ++h) {
+                        const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h < PER - 1 ? h : PER - 1;
+                        const int blk = kx * 3 + 2 - (h - rlo);
+                        mma_op<IN8>(d + (uint32_t)rlo * N, hi | (uint64_t)(ak + (uint32_t)h * row16),
+                                    hi | (uint64_t)(bk + (uint32_t)blk * btap), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
+                    }
+                }
+            }
+    } else {
+        constexpr int NY = Sp::NY, NX = PAR >= 2 ? 2 : 1;
+        const uint32_t plane16 = s.plane >> 4;
+        const uint32_t id2 = idesc_n(q.idesc, 2 * N);
+        const int u0 = q.g * PER;
+        if (sg == 0) {
+            // skip operand: the fine pixel of class cx at tap (ky, kx) is x-offset dxf = cx +
+            // kx - 1 from 2X, i.e. plane dxf & 1, staged column 1 + (dxf >> 1).  With both x
+            // classes in the tile, dxf = 0 and 1 serve both classes with weight blocks
+            // (ky, dxf) and (ky, dxf + 1), adjacent in shared memory, into the unit's two
+            // adjacent accumulators [cx = 1, cx = 0]: one MMA of 2N columns.
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int k = 0; k < NK; ++k)
+#pragma unroll
+                    for (int uu = 0; uu < PER; ++uu) {
+                        const int u = u0 + uu;
+                        const int r = u / NY, cy = PAR == 4 ? u - r * NY : q.py;
+                        const uint32_t du = d0 + (uint32_t)(u * NX) * N;
+                        const uint32_t ar = a0 + (uint32_t)((PAR == 4 ? cy : 0) + ky + 2 * r) * row16 + 2 * k;
+                        auto A = [&](int dxf) {
+                            return hi | (uint64_t)(ar + (uint32_t)(dxf & 1) * plane16 + (uint32_t)(1 + (dxf >> 1)) * pitch16);
+                        };
+                        const uint32_t bk = b0 + (uint32_t)(3 * ky) * btap + 2 * k;
+                        const uint32_t init = (first && ky == 0 && k == 0) ? 0u : 1u;
+                        if (NX == 2) {
+                            mma_op<IN8>(du, A(0), hi | (uint64_t)bk, id2, init);
+                            mma_op<IN8>(du, A(1), hi | (uint64_t)(bk + btap), id2, 1u);
+                            mma_op<IN8>(du + N, A(-1), hi | (uint64_t)bk, q.idesc, 1u);
+                            mma_op<IN8>(du, A(2), hi | (uint64_t)(bk + 2 * btap), q.idesc, 1u);
+                        } else {
+                            mma_op<IN8>(du, A(q.px - 1), hi | (uint64_t)bk, q.idesc, init);
+                            mma_op<IN8>(du, A(q.px), hi | (uint64_t)(bk + btap), q.idesc, 1u);
+                            mma_op<IN8>(du, A(q.px + 1), hi | (uint64_t)(bk + 2 * btap), q.idesc, 1u);
+                        }
+                    }
+        } else {
+            // nearest-upsampled operand: class (cx, cy) reads coarse rows cy - 1 + j (j = 0,
+            // 1) and columns dxc in {cx - 1, cx}, each with the sum of the 3x3 taps that land
+            // on that coarse pixel (blocks per (cy, j): [cx=1 dxc=+1][cx=1 dxc=0][cx=0 dxc=0]
+            // [cx=0 dxc=-1]); dxc = 0 serves both x classes with one MMA of 2N columns.
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k = 0; k < NK; ++k)
+#pragma unroll
+                    for (int uu = 0; uu < PER; ++uu) {
+                        const int u = u0 + uu;
+                        const int r = u / NY, cy = PAR == 4 ? u - r * NY : q.py;
+                        const uint32_t du = d0 + (uint32_t)(u * NX) * N;
+                        const uint32_t ar = a0 + (uint32_t)(r + cy + j) * row16 + 2 * k;
+                        const uint32_t bj = b0 + (uint32_t)((PAR == 4 ? 8 * cy : 0) + 4 * j) * btap + 2 * k;
+                        if (NX == 2) {
+                            mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, q.idesc, 1u);
+                            mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), id2, 1u);
+                            mma_op<IN8>(du + N, hi | (uint64_t)ar, hi | (uint64_t)(bj + 3 * btap), q.idesc, 1u);
+                        } else {
+                            // one class: cx = 1 uses blocks 0, 1 at columns +1, 0; cx = 0 blocks 2, 3 at 0, -1
+                            const uint32_t c1 = q.px ? 2 * pitch16 : pitch16;
+                            const uint32_t bb = bj + (q.px ? 0u : 2 * btap);
+                            mma_op<IN8>(du, hi | (uint64_t)(ar + c1), hi | (uint64_t)bb, q.idesc, 1u);
+                            mma_op<IN8>(du, hi | (uint64_t)(ar + c1 - pitch16), hi | (uint64_t)(bb + btap), q.idesc, 1u);
+                        }
+                    }
+        }
+    }
+}
+
 // PAR = 0: standard tiles of R rows x 128 columns.  PAR = 1, 2 or 4: the decoder's first
 // conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
@@ -529,8 +672,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
     const uint32_t drain = bars + 8u * (2 * S + 4);
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
-    float* sbias = reinterpret_cast<float*>(gbase + (tslot - base) + 16);
-    float* sscale = sbias + p.N;          // accumulator scale per output channel
+    // per-channel epilogue constants, 16-byte aligned for float4 reads (N is a multiple of 16)
+    float* sbias = reinterpret_cast<float*>(gbase + ((tslot - base + 8 + 15) & ~15u));
+    float* sscale = sbias + p.N;          // accumulator scale per output channel (E4M3 operands)
     float* shw = sscale + p.N;            // head weights [head_o][N], then head bias
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
@@ -618,15 +762,17 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         // classes (adjacent in TMEM, cx = 1 first).  Descriptors are built once per stage;
         // every tap, row and K step only adds a constant to the start-address field
         // (address >> 4, 14 bits).
-        constexpr int NY = PAR == 4 ? 2 : 1, NX = PAR >= 2 ? 2 : 1;
-        const int g = warp - 1, nunit = NY * R;
-        const int a_lo = g * nunit / p.nmma, a_hi = (g + 1) * nunit / p.nmma - 1;
-        const uint32_t idesc2 = (p.idesc & ~(0x3Fu << 17)) | ((uint32_t)(2 * N >> 3) << 17);
+        IssueCtx q;
+        q.g = warp - 1;
+        q.N = (uint32_t)N;
+        q.idesc = p.idesc;
         int use = 0, tcount = 0;
         bool ok = true, issued = false;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
             tile_of(t, n, x0, y0, px, py);
+            q.px = px;
+            q.py = py;
             const int b = tcount & 1;
             if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
@@ -634,101 +780,17 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
             const uint32_t d0 = tmem + (uint32_t)(b * NACC * N);
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
-                const uint32_t pitch16 = s.pitch >> 4, row16 = kHaloW * pitch16;
-                const uint64_t hi = sdesc_hi(8 * s.pitch, s.swz);
                 const int nk = (int)(s.pitch >> 5);  // one MMA per 32 bytes of K (16 BF16 or 32 E4M3)
-                const bool skip = PAR && sg == 0;
-                const uint32_t plane16 = s.plane >> 4;
-                const uint32_t btap = (uint32_t)N * pitch16;
                 for (int cc = 0; cc < s.nchunk; ++cc) {
                     const int st = use % S;
                     if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
                     const uint32_t b0 = a0 + (s.b_off >> 4);
-                    if (PAR == 0) {
-                        // Halo row h shifted by kx feeds output rows r = h - ky, ky = 0..2.
-                        // Up to wmax consecutive rows of this issuer go into one MMA: their
-                        // accumulators are adjacent in TMEM and their weight blocks
-                        // [kx][ky = 2,1,0] adjacent in shared memory, so N = rows * Cout.
-                        const int wmax = p.wmax;
-                        const uint32_t idesc0 = p.idesc & ~(0x3Fu << 17);
-                        for (int kx = 0; kx < 3; ++kx)
-                            for (int k = 0; k < nk; ++k) {
-                                const bool init = cc == 0 && kx == 0 && k == 0;  // first touch of every row
-                                for (int h = a_lo; h < a_hi + 3; ++h) {
-                                    const int rlo = h - 2 > a_lo ? h - 2 : a_lo, rhi = h < a_hi ? h : a_hi;
-                                    const uint64_t ad = hi | (uint64_t)(a0 + h * row16 + kx * pitch16 + 2 * k);
-                                    if (init) {  // one row per MMA, zeroing each accumulator at ky = 0
-                                        for (int r = rlo; r <= rhi; ++r) {
-                                            const int blk = kx * 3 + (2 - (h - r));
-                                            mma_op<IN8>(d0 + (uint32_t)(r * N), ad,
-                                                     hi | (uint64_t)(b0 + blk * btap + 2 * k), p.idesc, h == r ? 0u : 1u);
-                                        }
-                                        continue;
-                                    }
-                                    for (int r0 = rlo; r0 <= rhi; r0 += wmax) {
-                                        const int r1 = r0 + wmax - 1 < rhi ? r0 + wmax - 1 : rhi;
-                                        const int blk = kx * 3 + (2 - (h - r0));
-                                        const uint32_t nn = (uint32_t)((r1 - r0 + 1) * N);
-                                        mma_op<IN8>(d0 + (uint32_t)(r0 * N), ad, hi | (uint64_t)(b0 + blk * btap + 2 * k),
-                                                 idesc0 | ((nn >> 3) << 17), 1u);
-                                    }
-                                }
-                            }
-                    } else if (skip) {
-                        // decoder concat conv, skip operand: the fine pixel of class cx at tap
-                        // (ky, kx) is x-offset dxf = cx + kx - 1 from 2X, i.e. plane dxf & 1,
-                        // staged column 1 + (dxf >> 1).  With both x classes in the tile, the
-                        // offsets dxf = 0 and 1 serve both classes with weight blocks (ky, dxf)
-                        // and (ky, dxf + 1), adjacent in shared memory, into the unit's two
-                        // adjacent accumulators [cx = 1, cx = 0]: one MMA of 2N columns.
-                        for (int ky = 0; ky < 3; ++ky)
-                            for (int k = 0; k < nk; ++k)
-                                for (int u = a_lo; u <= a_hi; ++u) {
-                                    const int r = u / NY, cy = PAR == 4 ? u - r * NY : py;
-                                    const uint32_t du = d0 + (uint32_t)(u * NX * N);
-                                    const uint32_t ar = a0 + (uint32_t)((PAR == 4 ? cy : 0) + ky + 2 * r) * row16 + 2 * k;
-                                    auto A = [&](int dxf) {
-                                        return hi | (uint64_t)(ar + (uint32_t)(dxf & 1) * plane16 + (uint32_t)(1 + (dxf >> 1)) * pitch16);
-                                    };
-                                    const uint32_t bk = b0 + (uint32_t)(3 * ky) * btap + 2 * k;
-                                    if (NX == 2) {
-                                        mma_op<IN8>(du, A(0), hi | (uint64_t)bk, idesc2, (cc | ky | k) ? 1u : 0u);
-                                        mma_op<IN8>(du, A(1), hi | (uint64_t)(bk + btap), idesc2, 1u);
-                                        mma_op<IN8>(du + (uint32_t)N, A(-1), hi | (uint64_t)bk, p.idesc, 1u);
-                                        mma_op<IN8>(du, A(2), hi | (uint64_t)(bk + 2 * btap), p.idesc, 1u);
-                                    } else {
-                                        for (int kx = 0; kx < 3; ++kx)
-                                            mma_op<IN8>(du, A(px + kx - 1), hi | (uint64_t)(bk + kx * btap), p.idesc,
-                                                        (cc | ky | k | kx) ? 1u : 0u);
-                                    }
-                                }
-                    } else {
-                        // decoder concat conv, nearest-upsampled operand: class (cx, cy) reads
-                        // coarse rows cy - 1 + j (j = 0, 1) and columns dxc in {cx - 1, cx},
-                        // each with the sum of the 3x3 taps that land on that coarse pixel
-                        // (blocks per (cy, j): [cx=1 dxc=+1][cx=1 dxc=0][cx=0 dxc=0][cx=0 dxc=-1]);
-                        // dxc = 0 serves both x classes with one MMA of 2N columns.
-                        for (int j = 0; j < 2; ++j)
-                            for (int k = 0; k < nk; ++k)
-                                for (int u = a_lo; u <= a_hi; ++u) {
-                                    const int r = u / NY, cy = PAR == 4 ? u - r * NY : py;
-                                    const uint32_t du = d0 + (uint32_t)(u * NX * N);
-                                    const uint32_t ar = a0 + (uint32_t)(1 + r + cy - 1 + j) * row16 + 2 * k;
-                                    const uint32_t bj = b0 + (uint32_t)((PAR == 4 ? 8 * cy : 0) + 4 * j) * btap + 2 * k;
-                                    if (NX == 2) {
-                                        mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, p.idesc, 1u);
-                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), idesc2, 1u);
-                                        mma_op<IN8>(du + (uint32_t)N, hi | (uint64_t)ar, hi | (uint64_t)(bj + 3 * btap), p.idesc, 1u);
-                                    } else if (px == 1) {
-                                        mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, p.idesc, 1u);
-                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), p.idesc, 1u);
-                                    } else {
-                                        mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + 2 * btap), p.idesc, 1u);
-                                        mma_op<IN8>(du, hi | (uint64_t)ar, hi | (uint64_t)(bj + 3 * btap), p.idesc, 1u);
-                                    }
-                                }
+                    switch (nk) {
+                        case 1: issue_stage<R, PAR, IN8, 1>(q, sg, a0, b0, s, d0, cc == 0); break;
+                        case 2: issue_stage<R, PAR, IN8, 2>(q, sg, a0, b0, s, d0, cc == 0); break;
+                        default: issue_stage<R, PAR, IN8, 4>(q, sg, a0, b0, s, d0, cc == 0); break;
                     }
                     issued = true;
                     mma_commit(empty(st));
@@ -750,6 +812,25 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         const bool leader = threadIdx.x == 32 * (kMmaWarps + 1);
         const int Wh = p.W >> 1, Hh = p.H >> 1;
         const bool pool = p.pool_out != nullptr;
+        // bias (+ per-channel scale of E4M3 operands) and ReLU of 16 accumulator columns
+        auto act16 = [&](const uint32_t (&u)[16], int c, float (&f)[16]) {
+            const float4* b4 = reinterpret_cast<const float4*>(sbias + c);
+            const float4* s4 = reinterpret_cast<const float4*>(sscale + c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 bv = b4[j];
+                const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+                if (IN8) {
+                    const float4 sv = s4[j];
+                    const float ss[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) f[4 * j + i] = fmaxf(fmaf(__uint_as_float(u[4 * j + i]), ss[i], bb[i]), 0.f);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) f[4 * j + i] = fmaxf(__uint_as_float(u[4 * j + i]) + bb[i], 0.f);
+                }
+            }
+        };
         int tcount = 0;
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
             const int b = tcount & 1;
@@ -774,11 +855,10 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         tmem_wait16(u0);
                         tmem_wait16(u1);
                         float f0[16], f1[16], pm[16];
+                        act16(u0, c0, f0);
+                        act16(u1, c0, f1);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float bj = sbias[c0 + j], sj = sscale[c0 + j];
-                            f0[j] = fmaxf(fmaf(__uint_as_float(u0[j]), sj, bj), 0.f);
-                            f1[j] = fmaxf(fmaf(__uint_as_float(u1[j]), sj, bj), 0.f);
                             const float a = fmaxf(f0[j], f1[j]);
                             pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                         }
@@ -826,21 +906,31 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         tmem_wait16(u0);
                         if (two) tmem_wait16(u1);
                         float f0[16], f1[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            f0[j] = fmaxf(fmaf(__uint_as_float(u0[j]), sscale[c0 + j], sbias[c0 + j]), 0.f);
-                            f1[j] = two ? fmaxf(fmaf(__uint_as_float(u1[j]), sscale[c0 + 16 + j], sbias[c0 + 16 + j]), 0.f)
-                                        : 0.f;
-                        }
+                        act16(u0, c0, f0);
+                        if (two) act16(u1, c0 + 16, f1);
                         if (p.head_out) {
 #pragma unroll
                             for (int o = 0; o < 4; ++o) {  // head_o <= 4: h stays in registers
                                 if (o >= p.head_o) break;
+                                const float4* w4 = reinterpret_cast<const float4*>(shw + o * N + c0);
                                 float sacc = 0.f;
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    sacc = fmaf(shw[o * N + c0 + j], f0[j], sacc);
-                                    if (two) sacc = fmaf(shw[o * N + c0 + 16 + j], f1[j], sacc);
+                                for (int j = 0; j < 4; ++j) {
+                                    const float4 wv = w4[j];
+                                    sacc = fmaf(wv.x, f0[4 * j], sacc);
+                                    sacc = fmaf(wv.y, f0[4 * j + 1], sacc);
+                                    sacc = fmaf(wv.z, f0[4 * j + 2], sacc);
+                                    sacc = fmaf(wv.w, f0[4 * j + 3], sacc);
+                                }
+                                if (two) {
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j) {
+                                        const float4 wv = w4[4 + j];
+                                        sacc = fmaf(wv.x, f1[4 * j], sacc);
+                                        sacc = fmaf(wv.y, f1[4 * j + 1], sacc);
+                                        sacc = fmaf(wv.z, f1[4 * j + 2], sacc);
+                                        sacc = fmaf(wv.w, f1[4 * j + 3], sacc);
+                                    }
                                 }
                                 h[o] += sacc;
                             }

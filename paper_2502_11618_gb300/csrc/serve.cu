@@ -45,6 +45,77 @@ struct PinnedPool {
     }
 };
 
+// Host copy of finished results into the caller's buffer, split across a few persistent
+// worker threads: one 1080p RGB frame is 24.9 MB, and a single core's memcpy (~16-27 GB/s
+// on the Grace host) would otherwise cap a polling thread near 600 frames/s.
+struct CopyPool {
+    struct Part {
+        char* dst;
+        const char* src;
+        size_t n;
+        std::atomic<int>* left;
+    };
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<Part> q;
+    bool stop = false;
+
+    void start() {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int n = (int)std::min(7u, hw > 1 ? hw - 1 : 0u);
+        for (int i = 0; i < n; ++i)
+            th.emplace_back([this] {
+                std::unique_lock<std::mutex> lk(mu);
+                for (;;) {
+                    cv.wait(lk, [this] { return stop || !q.empty(); });
+                    if (q.empty()) return;  // stop requested and nothing left
+                    Part pt = q.front();
+                    q.pop_front();
+                    lk.unlock();
+                    std::memcpy(pt.dst, pt.src, pt.n);
+                    lk.lock();
+                    pt.left->fetch_sub(1);
+                    done_cv.notify_all();
+                }
+            });
+    }
+    void finish() {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto& t : th) t.join();
+        th.clear();
+    }
+    // Copies n bytes; returns when every part is done.  Parts of at least 2 MB, one done by
+    // the calling thread.
+    void copy(void* dst, const void* src, size_t n) {
+        const size_t kMin = 2u << 20;
+        const int parts = (int)std::min<size_t>(th.size() + 1, std::max<size_t>(1, n / kMin));
+        if (parts <= 1) {
+            std::memcpy(dst, src, n);
+            return;
+        }
+        const size_t step = (n / parts + 63) & ~(size_t)63;
+        std::atomic<int> left(0);
+        {
+            std::lock_guard<std::mutex> g(mu);
+            for (int i = 1; i < parts; ++i) {
+                const size_t off = step * i;
+                if (off >= n) break;
+                left.fetch_add(1);
+                q.push_back({static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, std::min(step, n - off), &left});
+            }
+        }
+        cv.notify_all();
+        std::memcpy(dst, src, std::min(step, n));
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return left.load() == 0; });
+    }
+};
+
 struct ServeReq {
     lnr_view view;
     lnr_intrinsics intr;
@@ -69,6 +140,7 @@ struct Server {
     uint64_t next_ticket = 1;
     size_t inflight = 0;
     PinnedPool pool;
+    CopyPool copier;
     lnr_precision prec = LNR_FP32;
     // stats
     uint64_t n_done = 0, n_launch = 0, max_b = 0, peak_bytes = 0;
@@ -229,6 +301,7 @@ lnr_status lnr_serve_start(lnr_ctx* c, int max_batch, int nslots) {
         s->slots.push_back(std::move(sl));
     }
     c->server = s;
+    s->copier.start();
     s->th = std::thread([s] { s->loop(); });
     return LNR_OK;
 }
@@ -240,6 +313,7 @@ lnr_status lnr_serve_stop(lnr_ctx* c) {
     s->stop = true;
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();
+    s->copier.finish();
     lnr_status st = LNR_OK;
     cudaSetDevice(c->device);
     const double deadline = now_s() + 10.0;
@@ -308,7 +382,7 @@ lnr_status lnr_poll(lnr_ctx* c, uint64_t ticket, float* out, double* latency_s) 
     }
     lnr_status st = LNR_OK;
     if (r.failed) st = fail(c, LNR_E_CUDA, "request failed: " + s->err);
-    else if (out && r.host) std::memcpy(out, r.host, r.bytes);
+    else if (out && r.host) s->copier.copy(out, r.host, r.bytes);
     if (latency_s) *latency_s = r.t_done - r.t_submit;
     if (r.host) {
         std::lock_guard<std::mutex> g(s->mu);
