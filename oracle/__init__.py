@@ -36,6 +36,9 @@ def lib():
         L.orc_cull.restype = C.c_int64
         L.orc_splat.argtypes = [p, p, p, p, p, p, p, p, p, p, p, C.c_int, C.c_int, p]
         L.orc_splat.restype = C.c_uint64
+        L.orc_soft_colours.argtypes = [p, p, p, p, p, p, p, p, p, p, p, p, C.c_int, C.c_int, p,
+                                       C.c_float, p]
+        L.orc_soft_colours.restype = None
         L.orc_resolve.argtypes = [p, p, C.c_int, C.c_int, p, p, p]
         L.orc_resolve.restype = None
         L.orc_minpool.argtypes = [p, C.c_int, C.c_int, p]
@@ -145,6 +148,20 @@ def splat(grid: Grid, vp: ViewParams, intr, W, H, visible=None):
     return keys, int(nvis)
 
 
+def soft_colours(grid: Grid, vp: ViewParams, intr, W, H, keys, rel, visible=None):
+    """Soft z-buffer colours (H, W, 3) uint8: per pixel the integer mean (rounded half up)
+    of the colours of the points with z <= z_front * (1 + rel), z_front from keys."""
+    rgb = np.zeros(W * H * 3, np.uint8)
+    ia = intr_array(intr)
+    vis = None if visible is None else _c(visible, np.uint8)
+    scale = np.float32(1.0) + np.float32(rel)
+    lib().orc_soft_colours(_ptr(vis), _ptr(grid.dims), _ptr(grid.cell_start), _ptr(grid.ox),
+                           _ptr(grid.oy), _ptr(grid.oz), _ptr(grid.rgbs), _ptr(vp.anchor),
+                           _ptr(vp.d0), _ptr(vp.s), _ptr(vp.Rf), _ptr(ia), W, H,
+                           _ptr(_c(keys, np.uint64)), float(scale), _ptr(rgb))
+    return rgb.reshape(H, W, 3)
+
+
 def resolve(keys, rgbs, W, H):
     rgb = np.zeros(W * H * 3, np.uint8)
     D = np.zeros(W * H, np.float32)
@@ -214,13 +231,16 @@ def num_threads():
 
 
 def render(grid: Grid, view, intr, W, H, n_levels, fs, weights=None, ch=None, has_bn=False,
-           brute=False):
+           brute=False, soft=0.0):
     """Every stage of one frame: keys, RGBDA before the filter, kept depth, U-Net input
-    and (with weights) the FP64 output image."""
+    and (with weights) the FP64 output image.  soft > 0: soft z-buffer colours with
+    relative depth threshold `soft`."""
     vp = view_params(grid, view.R, view.C)
     vis, nvis_cells = (None, grid.n_cells) if brute else cull(grid, vp, intr, W, H)
     keys, n_vis_points = splat(grid, vp, intr, W, H, vis)
     rgb, D, A = resolve(keys, grid.rgbs, W, H)
+    if soft > 0:
+        rgb = soft_colours(grid, vp, intr, W, H, keys, soft, vis)
     U0 = depth_filter(D, n_levels, fs)
     x = pack_input(rgb, U0, intr.zfar)
     out = dict(vp=vp, visible=vis, n_vis_cells=nvis_cells, n_vis_points=n_vis_points,

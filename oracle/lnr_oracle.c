@@ -14,6 +14,8 @@
  *   cull      frustum culling of grid cells, six planes       (Sec. 3; Fig. 1)
  *   splat     1x1-pixel projection with a hard z-buffer keyed by (depth, position)
  *                                                             (Sec. 3, projection)
+ *   soft      soft z-buffer: the colours of the points that arrive within a small
+ *             depth threshold of the front are averaged       (Sec. 3, projection)
  *   resolve   RGB, depth D and fill mask A                    (Fig. 1; Sec. 3 "U-Net")
  *   filter    min-pool pyramid, then Laplacian-edge-aware upsampling with
  *             filter_strength and linear-interpolation fill   (Fig. 2; Sec. 3, "Depth
@@ -24,8 +26,10 @@
  *             convolution                                      (Fig. 1; Sec. 3, "U-Net")
  *
  * Readings where the paper is silent (each also listed in the design notes):
- *   - hard z-buffer (the paper averages colours within a depth threshold); ties in depth
- *     break towards the lower sorted position;
+ *   - the front of a pixel is its hard z-buffer minimum (ties in depth break towards the
+ *     lower sorted position); with the soft rule a point of the pixel contributes its
+ *     colour when z <= z_front * (1 + rel) in FP32 (rel unstated; 0.01 by default in
+ *     the tests), and the colour is the per-channel integer mean rounded half up;
  *   - D is view-space z; the U-Net's D channel is z / zfar;
  *   - the Laplacian is the 4-neighbour kernel on the coarser min-pooled level with
  *     replicated borders, and a pixel is an edge when |lap| > EDGE_REL * depth;
@@ -210,6 +214,27 @@ static uint32_t fbits(float f) {
     return u;
 }
 
+/* Pixel of the point at sorted position pos of a cell whose camera-space origin is o:
+ * -1 when it falls outside the near/far range or the image; its depth in *zout. */
+static int64_t point_pixel(const float o[3], const float* ox, const float* oy, const float* oz,
+                           uint32_t pos, const float Rf[9], const float intr[6], int W, int H,
+                           float* zout) {
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], zn = intr[4], zf = intr[5];
+    float p[3];
+    for (int r = 0; r < 3; ++r) {
+        float t = fmaf(Rf[3 * r + 2], oz[pos], o[r]);
+        t = fmaf(Rf[3 * r + 1], oy[pos], t);
+        p[r] = fmaf(Rf[3 * r + 0], ox[pos], t);
+    }
+    float z = p[2];
+    if (!(z > zn && z < zf)) return -1;
+    float u = (fx * p[0]) / z + cx;
+    float v = (fy * p[1]) / z + cy;
+    if (!(u >= 0.0f && u < (float)W && v >= 0.0f && v < (float)H)) return -1;
+    *zout = z;
+    return (int64_t)floorf(v) * W + (int64_t)floorf(u);
+}
+
 /* keys[v*W+u] = min over the points of the visible cells (all cells when visible is
  * NULL) that project to pixel (u,v) of (bits(z) << 32 | pos); ~0 where none does.
  * Returns the number of points in the visited cells. */
@@ -217,8 +242,6 @@ uint64_t orc_splat(const uint8_t* visible, const int32_t dims[3], const uint32_t
                    const float* ox, const float* oy, const float* oz, const int32_t anchor[3],
                    const float d0[3], const float s[9], const float Rf[9], const float intr[6],
                    int W, int H, uint64_t* keys) {
-    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], zn = intr[4], zf = intr[5];
-    const float Wf = (float)W, Hf = (float)H;
     for (int64_t q = 0; q < (int64_t)W * H; ++q) keys[q] = ~(uint64_t)0;
     uint64_t nvis = 0;
     for (int64_t k = 0; k < dims[2]; ++k)
@@ -230,23 +253,58 @@ uint64_t orc_splat(const uint8_t* visible, const int32_t dims[3], const uint32_t
                 cam_of(i, j, k, anchor, d0, s, 0.0f, 0.0f, 0.0f, o);
                 nvis += cell_start[c + 1] - cell_start[c];
                 for (uint32_t pos = cell_start[c]; pos < cell_start[c + 1]; ++pos) {
-                    float p[3];
-                    for (int r = 0; r < 3; ++r) {
-                        float t = fmaf(Rf[3 * r + 2], oz[pos], o[r]);
-                        t = fmaf(Rf[3 * r + 1], oy[pos], t);
-                        p[r] = fmaf(Rf[3 * r + 0], ox[pos], t);
-                    }
-                    float z = p[2];
-                    if (!(z > zn && z < zf)) continue;
-                    float u = (fx * p[0]) / z + cx;
-                    float v = (fy * p[1]) / z + cy;
-                    if (!(u >= 0.0f && u < Wf && v >= 0.0f && v < Hf)) continue;
-                    int64_t pix = (int64_t)floorf(v) * W + (int64_t)floorf(u);
+                    float z;
+                    int64_t pix = point_pixel(o, ox, oy, oz, pos, Rf, intr, W, H, &z);
+                    if (pix < 0) continue;
                     uint64_t key = ((uint64_t)fbits(z) << 32) | pos;
                     if (key < keys[pix]) keys[pix] = key;
                 }
             }
     return nvis;
+}
+
+/* Soft z-buffer colours (Sec. 3, "Point Cloud Projection": colours of points that arrive
+ * at similar depths are averaged, given a small depth threshold).  keys are the hard
+ * z-buffer of the same points; a point projecting to pixel q contributes when its depth
+ * z <= z_front(q) * scale (one FP32 multiply, scale = 1 + rel), z_front the depth in
+ * keys[q].  rgb[q] = per-channel mean of the contributors, (sum + n/2) / n in integers;
+ * 0 where keys[q] is empty. */
+void orc_soft_colours(const uint8_t* visible, const int32_t dims[3], const uint32_t* cell_start,
+                      const float* ox, const float* oy, const float* oz, const uint32_t* rgbs,
+                      const int32_t anchor[3], const float d0[3], const float s[9],
+                      const float Rf[9], const float intr[6], int W, int H, const uint64_t* keys,
+                      float scale, uint8_t* rgb) {
+    const int64_t P = (int64_t)W * H;
+    uint64_t* sum = (uint64_t*)calloc((size_t)P * 4, sizeof(uint64_t));  /* r, g, b, n */
+    for (int64_t k = 0; k < dims[2]; ++k)
+        for (int64_t j = 0; j < dims[1]; ++j)
+            for (int64_t i = 0; i < dims[0]; ++i) {
+                int64_t c = (k * dims[1] + j) * dims[0] + i;
+                if (visible && !visible[c]) continue;
+                float o[3];
+                cam_of(i, j, k, anchor, d0, s, 0.0f, 0.0f, 0.0f, o);
+                for (uint32_t pos = cell_start[c]; pos < cell_start[c + 1]; ++pos) {
+                    float z;
+                    int64_t pix = point_pixel(o, ox, oy, oz, pos, Rf, intr, W, H, &z);
+                    if (pix < 0 || keys[pix] == ~(uint64_t)0) continue;
+                    uint32_t zb = (uint32_t)(keys[pix] >> 32);
+                    float zfront;
+                    memcpy(&zfront, &zb, 4);
+                    float thr = zfront * scale;
+                    if (!(z <= thr)) continue;
+                    uint32_t col = rgbs[pos];
+                    sum[4 * pix + 0] += col & 255u;
+                    sum[4 * pix + 1] += (col >> 8) & 255u;
+                    sum[4 * pix + 2] += (col >> 16) & 255u;
+                    sum[4 * pix + 3] += 1;
+                }
+            }
+    for (int64_t q = 0; q < P; ++q) {
+        uint64_t n = sum[4 * q + 3];
+        for (int ch = 0; ch < 3; ++ch)
+            rgb[3 * q + ch] = n ? (uint8_t)((sum[4 * q + ch] + n / 2) / n) : 0;
+    }
+    free(sum);
 }
 
 /* RGB, depth (+inf where empty) and fill mask from the z-buffer keys. */

@@ -170,6 +170,80 @@ def test_zbuffer_brute_force_with_ties_and_duplicates():
     assert checked > 200
 
 
+def _pixel_centre_point(intr, col, row, z):
+    """World point (camera at the origin, identity rotation) projecting to the centre of
+    pixel (col, row) at depth z."""
+    return np.array([(col + 0.5 - intr.cx) / intr.fx * z, (row + 0.5 - intr.cy) / intr.fy * z, z])
+
+
+def test_soft_zbuffer_hand_case():
+    """Soft z-buffer colours on a hand-built pixel (Sec. 3: colours of points arriving at
+    similar depths are averaged): contributors are the points within z_front * (1 + rel)."""
+    W, H = 64, 48
+    intr = synth.intrinsics_for(W, H)
+    pts = [(_pixel_centre_point(intr, 20, 10, 2.000), (10, 20, 30)),
+           (_pixel_centre_point(intr, 20, 10, 2.015), (20, 40, 61)),
+           (_pixel_centre_point(intr, 20, 10, 2.050), (250, 250, 250)),
+           (_pixel_centre_point(intr, 40, 30, 3.000), (7, 8, 9))]
+    xyz = np.round(np.array([p for p, _ in pts]) * 4096.0) / 4096.0
+    rgb = np.array([c for _, c in pts], np.uint8)
+    g = oracle.build_grid(xyz, rgb, None, 0.5)
+    vp = oracle.view_params(g, np.eye(3), np.zeros(3))
+    keys, _ = oracle.splat(g, vp, intr, W, H)
+    expect = {0.0: (10, 20, 30),        # only the front point
+              0.01: (15, 30, 46),       # front + 2.015 <= 2.02: (30 + 61 + 1) // 2 = 46
+              0.03: (93, 103, 114)}     # all three: (280 + 1) // 3, (310 + 1) // 3, (341 + 1) // 3
+    for rel, col in expect.items():
+        c = oracle.soft_colours(g, vp, intr, W, H, keys, rel)
+        assert tuple(int(v) for v in c[10, 20]) == col, rel
+        assert tuple(int(v) for v in c[30, 40]) == (7, 8, 9)
+        assert int(c.sum()) == sum(col) + 24          # every other pixel empty
+
+
+def test_soft_zero_threshold_without_ties_equals_hard():
+    """With rel = 0 and no two points at the same depth only the front point remains."""
+    rng = np.random.default_rng(21)
+    W, H = 40, 30
+    intr = synth.intrinsics_for(W, H)
+    n = 3000
+    xyz, rgb, scan = _tiny_cloud(n, rng, center_z=4.0, spread=1.2)
+    xyz[:, 2] = 3.0 + rng.permutation(n) / 4096.0          # distinct depths
+    g = oracle.build_grid(xyz, rgb, scan, 0.5)
+    vp = oracle.view_params(g, np.eye(3), np.zeros(3))
+    keys, _ = oracle.splat(g, vp, intr, W, H)
+    hard, _, A = oracle.resolve(keys, g.rgbs, W, H)
+    soft = oracle.soft_colours(g, vp, intr, W, H, keys, 0.0)
+    assert A.sum() > 500
+    assert np.array_equal(soft, hard)
+
+
+def test_soft_wide_threshold_is_mean_of_the_pixel():
+    """With a threshold wider than the scene every point of a pixel contributes: the
+    colour is the integer mean over the points the FP64 pinhole model puts there."""
+    rng = np.random.default_rng(22)
+    W, H = 32, 24
+    intr = synth.intrinsics_for(W, H)
+    xyz, rgb, scan = _tiny_cloud(4000, rng, center_z=4.0, spread=1.0)
+    g = oracle.build_grid(xyz, rgb, scan, 0.5)
+    vp = oracle.view_params(g, np.eye(3), np.zeros(3))
+    keys, _ = oracle.splat(g, vp, intr, W, H)
+    soft = oracle.soft_colours(g, vp, intr, W, H, keys, 1e6)
+    u, v, z = _pinhole64(xyz, np.eye(3), np.zeros(3), intr)
+    inside = (z > intr.znear) & (z < intr.zfar) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+    far_edge = (np.abs(u - np.round(u)) > 1e-3) & (np.abs(v - np.round(v)) > 1e-3)
+    pix = np.floor(v).astype(np.int64) * W + np.floor(u).astype(np.int64)
+    checked = 0
+    for q in range(W * H):
+        cand = np.nonzero(inside & (pix == q))[0]
+        if len(cand) < 2 or not far_edge[cand].all():
+            continue
+        n = len(cand)
+        mean = (rgb[cand].astype(np.int64).sum(0) + n // 2) // n
+        assert np.array_equal(soft.reshape(-1, 3)[q], mean), q
+        checked += 1
+    assert checked > 100
+
+
 def test_georeferencing_offset_is_bit_exact():
     """Translating cloud and camera by a large exact offset leaves every key unchanged."""
     s = synth.room_scene(n_points=30000, seed=4)
