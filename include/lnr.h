@@ -113,6 +113,15 @@ lnr_status lnr_set_unet(lnr_ctx* ctx, const lnr_unet_desc* desc, const float* we
  * LNR_E_STATE until the net is calibrated. */
 lnr_status lnr_set_precision(lnr_ctx* ctx, lnr_precision precision);
 
+/* Collision rule of the splat (Sec. 3, "Point Cloud Projection").  rel = 0 (the default):
+ * hard z-buffer, each pixel keeps its nearest point (depth ties: lower sorted position).
+ * rel > 0: soft z-buffer, the pixel's colour is the per-channel integer mean, rounded half
+ * up, of every point that projects to it with depth z <= z_front * (1 + rel) (one FP32
+ * multiply), z_front its nearest depth; depth and the filter are unchanged.  The paper
+ * states no threshold.  Costs a second pass over the visible points and 16 bytes per
+ * pixel.  Errors: LNR_E_ARG for rel negative, NaN or above 1e6; LNR_E_STATE while serving. */
+lnr_status lnr_set_soft_zbuffer(lnr_ctx* ctx, float rel);
+
 /* Render one frame (Fig. 1): cull, splat, filter (Fig. 2) with n_levels min-pool levels
  * and filter_strength fs, U-Net.  out_rgb: H*W*3 FP32 in [0, 1], HWC; host memory, or
  * device memory when out_on_device != 0 (then the call returns without waiting for the

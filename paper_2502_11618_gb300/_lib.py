@@ -25,7 +25,7 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
-           "lnr_filter_static", "lnr_autotune", "lnr_calibrate"]
+           "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer"]
 
 
 class LnrError(RuntimeError):
@@ -70,6 +70,7 @@ def lib():
             "lnr_grid_info": ([p, p, p], st),
             "lnr_set_unet": ([p, C.POINTER(UnetDesc), p, sz, i], st),
             "lnr_set_precision": ([p, i], st),
+            "lnr_set_soft_zbuffer": ([p, f], st),
             "lnr_render": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, i], st),
             "lnr_render_stage": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, i, p, i], st),
             "lnr_render_batch": ([p, i, p, p, i, i, i, p, p, i], st),
@@ -181,6 +182,11 @@ class Renderer:
     def autotune(self, W, H, batch=1):
         """Time every tensor-core conv configuration at (batch, W, H); keep the fastest."""
         self._check(self._L.lnr_autotune(self._c, int(W), int(H), int(batch)))
+
+    def set_soft_zbuffer(self, rel):
+        """0: hard z-buffer (default); rel > 0: soft z-buffer averaging the colours of the
+        points within z_front * (1 + rel) of each pixel's front."""
+        self._check(self._L.lnr_set_soft_zbuffer(self._c, float(rel)))
 
     def set_precision(self, precision):
         self._check(self._L.lnr_set_precision(self._c, PRECISIONS.get(precision, precision)))

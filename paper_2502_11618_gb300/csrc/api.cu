@@ -28,7 +28,7 @@ lnr_status cuda_fail(lnr_ctx* c, cudaError_t e, const char* where) {
 
 void Workspace::release() {
     DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_cell, &vis_pref, &vis_tot, &keys,
-                   &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
+                   &soft_acc, &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
     for (DBuf* b : all) b->release();
     for (auto& a : act) a.release();
     if (pinned_view.p) cudaFreeHost(pinned_view.p);
@@ -102,7 +102,8 @@ lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const
 static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int H, int nlev) {
     cudaError_t e;
     const void* before[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
-                            ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p};
+                            ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
+                            ws.soft_acc.p};
     const size_t P = (size_t)W * H;
     const int nb = cull_blocks(c->ncells);
     const size_t pf = pyramid_floats(W, H, kMaxLevels);
@@ -116,6 +117,11 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
     const bool new_keys = ws.keys.bytes < 8 * P * B;
     if ((e = ws.keys.ensure(8 * P * B))) return e;
     if (new_keys) ws.keys_dirty = true;
+    if (c->soft_rel > 0.0f) {
+        const bool new_acc = ws.soft_acc.bytes < 16 * P * B;
+        if ((e = ws.soft_acc.ensure(16 * P * B))) return e;
+        if (new_acc) ws.soft_dirty = true;
+    }
     if (ws.pinned_view.bytes < sizeof(ViewDev) * B) {
         if (ws.pinned_view.p) cudaFreeHost(ws.pinned_view.p);
         if ((e = cudaMallocHost(&ws.pinned_view.p, sizeof(ViewDev) * B))) return e;
@@ -125,7 +131,8 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
         for (auto& ev : ws.ev)
             if ((e = cudaEventCreate(&ev))) return e;
     const void* after[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
-                           ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p};
+                           ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
+                           ws.soft_acc.p};
     for (size_t i = 0; i < sizeof(before) / sizeof(before[0]); ++i)
         if (before[i] != after[i]) ws.alloc_gen++;
     ws.B = B;
@@ -155,6 +162,7 @@ void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_pr
         ws.keys_dirty = true;  // the resolve that would clear the keys does not run
         return;
     }
+    if (c->soft_rel > 0.0f) launch_splat_soft(c, ws, st);
     launch_resolve_pyramid(c, ws, st);
     mark(3);
     if (stage == LNR_STAGE_RGBDA_RAW) return;
@@ -189,10 +197,11 @@ lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views
     return LNR_OK;
 }
 
-size_t frame_bytes(int B, int W, int H) {
+size_t frame_bytes(int B, int W, int H, bool soft) {
     const size_t P = (size_t)B * W * H;
-    // keys 8, depth 4, rgba 4, kept depth 4, output 12, U-Net input 32 bytes per pixel, pyramid
-    return P * 64 + 8 * (size_t)B * pyramid_floats(W, H, kMaxLevels);
+    // keys 8, depth 4, rgba 4, kept depth 4, output 12, U-Net input 32 bytes per pixel, pyramid;
+    // soft z-buffer sums 16
+    return P * (soft ? 80 : 64) + 8 * (size_t)B * pyramid_floats(W, H, kMaxLevels);
 }
 
 // Enqueue a whole frame batch on ws.stream: replayed from a CUDA graph captured for this
@@ -481,6 +490,17 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
     if (prec == LNR_FP8) {  // E4M3 needs calibrated activation scales first
         c->prec = LNR_BF16;
         return fail(c, LNR_E_STATE, "FP8 needs lnr_calibrate after set_unet (BF16 selected meanwhile)");
+    }
+    return LNR_OK;
+}
+
+lnr_status lnr_set_soft_zbuffer(lnr_ctx* c, float rel) {
+    if (!c) return LNR_E_ARG;
+    if (!(rel >= 0.0f && rel <= 1e6f)) return fail(c, LNR_E_ARG, "soft z-buffer threshold must be in [0, 1e6]");
+    if (c->server) return fail(c, LNR_E_STATE, "cannot change the z-buffer rule while serving");
+    if (rel != c->soft_rel) {
+        c->soft_rel = rel;
+        c->cloud_gen++;  // captured frame graphs hold the other splat sequence
     }
     return LNR_OK;
 }

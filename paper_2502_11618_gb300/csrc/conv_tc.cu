@@ -38,11 +38,12 @@ namespace lnr {
 namespace {
 
 constexpr int kThreads = 192;
-// halo kernel: producer warp, kMmaWarps MMA-issuing warps, 4 epilogue warps.  One thread
+// halo kernel: producer warp, kMmaWarps MMA-issuing warps, kEpiWarps epilogue warps.  One thread
 // issues about one tcgen05.mma per ~120 cycles whatever N is, so small-N convolutions need
 // several issuing threads; each owns disjoint accumulators.
 constexpr int kMmaWarps = 4;
-constexpr int kHaloThreads = 32 * (1 + kMmaWarps + 4);
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter: one warp per scheduler cannot hide the epilogue's latency
+constexpr int kHaloThreads = 32 * (1 + kMmaWarps + kEpiWarps);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
 
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
     // per-channel epilogue constants, 16-byte aligned for float4 reads (N is a multiple of 16)
     float* sbias = reinterpret_cast<float*>(gbase + ((tslot - base + 8 + 15) & ~15u));
     float* sscale = sbias + p.N;          // accumulator scale per output channel (E4M3 operands)
-    float* shw = sscale + p.N;            // head weights [head_o][N], then head bias
+    float* shw = sscale + p.N;            // head weights [4][N] (zero past head_o), then 4 head biases
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
     if (threadIdx.x == 0) {
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull(b), p.nmma);
-            mbar_init(tempty(b), 4);
+            mbar_init(tempty(b), kEpiWarps);
         }
         mbar_init(drain, p.nmma);
         *flag = 0;
@@ -696,8 +697,10 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         sscale[i] = p.cscale ? p.cscale[i] : 1.0f;
     }
     if (p.head_out)
-        for (int i = threadIdx.x; i < p.head_o * (N + 1); i += kHaloThreads)
-            shw[i] = i < p.head_o * N ? p.head_w[i] : p.head_b[i - p.head_o * N];
+        for (int i = threadIdx.x; i < 4 * (N + 1); i += kHaloThreads) {
+            const int o = i < 4 * N ? i / N : i - 4 * N;
+            shw[i] = o >= p.head_o ? 0.f : i < 4 * N ? p.head_w[i] : p.head_b[o];
+        }
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
@@ -809,6 +812,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
         const int m = 32 * q + lane;
+        const int eh = (warp - kMmaWarps - 1) >> 2;  // which of the two warps of this lane quarter
         const bool leader = threadIdx.x == 32 * (kMmaWarps + 1);
         const int Wh = p.W >> 1, Hh = p.H >> 1;
         const bool pool = p.pool_out != nullptr;
@@ -835,7 +839,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
             const int b = tcount & 1;
             if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
-            named_sync(1, 128);
+            named_sync(1, 32 * kEpiWarps);
             if (*flag) break;
             tc_fence_after();
             int n, x0, y0, px, py;
@@ -843,9 +847,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
             constexpr int NCE = PAR == 0 ? 1 : PAR;
             const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NCE * R * N);
             if (pool) {
-                // rows in pairs: both rows stored, their 2x2 maximum pooled with the lane
-                // that holds the neighbouring column
-                for (int r = 0; r < R; r += 2) {
+                // rows in pairs (pairs alternate between the quarter's two warps): both rows
+                // stored, their 2x2 maximum pooled with the lane holding the next column
+                for (int r = 2 * eh; r < R; r += 4) {
                     const int x = x0 + m, y = y0 + r;
                     const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
                     for (int c0 = 0; c0 < N; c0 += 16) {
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     }
                 }
             } else {
-                for (int a = 0; a < NCE * R; ++a) {
+                for (int a = eh; a < NCE * R; a += 2) {
                     int x, y;
                     bool v;
                     if (PAR) {
@@ -910,8 +914,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         if (two) act16(u1, c0 + 16, f1);
                         if (p.head_out) {
 #pragma unroll
-                            for (int o = 0; o < 4; ++o) {  // head_o <= 4: h stays in registers
-                                if (o >= p.head_o) break;
+                            for (int o = 0; o < 4; ++o) {  // 4 independent chains (zero weights past head_o)
                                 const float4* w4 = reinterpret_cast<const float4*>(shw + o * N + c0);
                                 float sacc = 0.f;
 #pragma unroll
@@ -948,7 +951,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
 #pragma unroll
                         for (int o = 0; o < 4; ++o) {
                             if (o >= p.head_o) break;
-                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[p.head_o * N + o])));
+                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[4 * N + o])));
                         }
                     }
                 }
@@ -1436,7 +1439,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_o = head_o;
     p.err = g_err;
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 +
-                        4 * (size_t)(2 * N + head_o * (N + 1));
+                        4 * (size_t)(2 * N + (head_out ? 4 * (N + 1) : 0));
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams)) {
         static std::mutex mu;

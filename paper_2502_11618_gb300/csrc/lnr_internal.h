@@ -119,6 +119,8 @@ struct Workspace {
     DBuf vis_cell, vis_pref, vis_tot;       // compacted visible cells, point prefix, totals
     DBuf keys;                              // uint64 [B][P]
     bool keys_dirty = true;
+    DBuf soft_acc;                          // soft z-buffer sums, uint64 [B][P][2] (soft mode only)
+    bool soft_dirty = true;
     DBuf depth, rgba;                       // float / uint32 [B][P]
     DBuf pyr_m, pyr_u;                      // min-pooled and upsampled levels (all levels)
     DBuf u0;                                // float [B][P] kept depth (stage tap)
@@ -174,6 +176,8 @@ struct lnr_ctx {
     lnr::Unet unet;
     lnr_precision prec = LNR_FP32;
     uint64_t unet_gen = 0;
+    // splat collision rule: 0 = hard z-buffer, > 0 = soft with this relative depth threshold
+    float soft_rel = 0.0f;
     // per-frame workspace of the synchronous calls
     lnr::Workspace ws;
     bool timing = false;
@@ -199,6 +203,7 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_clear_keys(Workspace& ws, cudaStream_t st);
 void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
 // unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC16, 2 = none (stage taps only).
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,
@@ -214,7 +219,7 @@ lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views
                          int H, int nlev, const float* fs);
 void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec, bool timed);
 cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph);
-size_t frame_bytes(int B, int W, int H);  // raster workspace bytes of a batch
+size_t frame_bytes(int B, int W, int H, bool soft);  // raster workspace bytes of a batch
 
 // unet.cu
 lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps);

@@ -204,11 +204,19 @@ struct __align__(16) ChunkCell {
     uint32_t base;   // sorted position of its first point minus pref (mod 2^32)
 };
 
+// SOFT = false: hard z-buffer pass, atomicMin of (bits(z) << 32 | position) per pixel.
+// SOFT = true: second pass of the soft z-buffer (Sec. 3: colours of points arriving at
+// similar depths are averaged): every point whose depth is within z_front * scale (one
+// FP32 multiply) of its pixel's front, read from the finished keys, adds its colour and a
+// count to the pixel's integer sums -- acc[2q] = r << 32 | g, acc[2q+1] = b << 32 | n --
+// so the result does not depend on the order of the atomics.
+template <bool SOFT>
 __global__ void __launch_bounds__(kSplatThreads) k_splat(
     const ViewDev* __restrict__ views, const uint32_t* __restrict__ cell_start, int dx, int dy,
     int64_t C, const uint32_t* __restrict__ vis_cell, const uint32_t* __restrict__ vis_pref,
     const uint32_t* __restrict__ tot, const float* __restrict__ ox, const float* __restrict__ oy,
-    const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys) {
+    const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys,
+    const uint32_t* __restrict__ rgbs, unsigned long long* __restrict__ acc, float scale) {
     __shared__ ChunkCell cells[kSplatChunk];
     __shared__ int s_vc0, s_nc;
     const int view = blockIdx.y;
@@ -275,8 +283,17 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
             const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
             if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
             const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
-            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos;
-            atomicMin(&kv[pix], key);
+            if (!SOFT) {
+                const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos;
+                atomicMin(&kv[pix], key);
+            } else {
+                const unsigned long long front = kv[pix];
+                if (front == kEmpty || !(z <= __fmul_rn(__uint_as_float((uint32_t)(front >> 32)), scale))) continue;
+                const uint32_t col = rgbs[pos];
+                unsigned long long* a = acc + 2 * ((size_t)view * W * H + pix);
+                atomicAdd(a, ((unsigned long long)(col & 255u) << 32) | ((col >> 8) & 255u));
+                atomicAdd(a + 1, ((unsigned long long)((col >> 16) & 255u) << 32) | 1ull);
+            }
         }
         __syncthreads();
     }
@@ -292,10 +309,13 @@ __global__ void k_fill_u64(unsigned long long* __restrict__ p, size_t n) {
 // One 64x64 tile: keys -> depth (+inf empty) and rgba (r | g<<8 | b<<16 | A<<24), keys
 // reset to empty for the next frame, then every min-pool level of the tile (kernel 2x2,
 // stride 2; level sizes ceil(W/2^l) x ceil(H/2^l); pixels outside the image count as
-// +inf, so each level pixel is the minimum over its clipped 2^l x 2^l block).
+// +inf, so each level pixel is the minimum over its clipped 2^l x 2^l block).  With the
+// soft z-buffer's sums (acc non-null) the colour is their per-channel integer mean
+// (sum + n/2) / n, and the sums are reset to zero.
 __global__ void __launch_bounds__(256) k_resolve_pyramid(
     unsigned long long* __restrict__ keys, const uint32_t* __restrict__ rgbs, int W, int H, int nlev,
-    float* __restrict__ depth, uint32_t* __restrict__ rgba, float* __restrict__ pyr, size_t pyr_stride) {
+    float* __restrict__ depth, uint32_t* __restrict__ rgba, float* __restrict__ pyr, size_t pyr_stride,
+    unsigned long long* __restrict__ acc) {
     __shared__ float s[64][65];
     __shared__ float t[32][33];
     const int view = blockIdx.z;
@@ -318,6 +338,17 @@ __global__ void __launch_bounds__(256) k_resolve_pyramid(
                 d = __uint_as_float((uint32_t)(key >> 32));
                 col = (rgbs[(uint32_t)key] & 0x00ffffffu) | (1u << 24);
                 kv[q] = kEmpty;
+                if (acc) {
+                    ulonglong2* a = reinterpret_cast<ulonglong2*>(acc) + view * P + q;
+                    const ulonglong2 sums = *a;
+                    const unsigned long long n = sums.y & 0xffffffffull;
+                    if (n) {
+                        const unsigned long long r = ((sums.x >> 32) + n / 2) / n, g = ((sums.x & 0xffffffffull) + n / 2) / n,
+                                                 b = ((sums.y >> 32) + n / 2) / n;
+                        col = (uint32_t)r | ((uint32_t)g << 8) | ((uint32_t)b << 16) | (1u << 24);
+                    }
+                    *a = make_ulonglong2(0ull, 0ull);
+                }
             }
             dv[q] = d;
             cv[q] = col;
@@ -520,11 +551,28 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
 void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
     int per_view = std::max(1, (c->num_sms * 8) / ws.B);
     dim3 g(per_view, ws.B);
-    k_splat<<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
-                                         c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
-                                         ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(), c->ox.as<float>(),
-                                         c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
-                                         ws.keys.as<unsigned long long>());
+    k_splat<false><<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
+                                                c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
+                                                ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
+                                                c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
+                                                ws.keys.as<unsigned long long>(), nullptr, nullptr, 1.0f);
+}
+
+// Second pass of the soft z-buffer (after launch_splat has finished the keys).
+void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
+    if (ws.soft_dirty) {  // fresh allocation: zero every sum once; the resolve re-zeroes what it reads
+        cudaMemsetAsync(ws.soft_acc.p, 0, ws.soft_acc.bytes, st);
+        ws.soft_dirty = false;
+    }
+    int per_view = std::max(1, (c->num_sms * 8) / ws.B);
+    dim3 g(per_view, ws.B);
+    const float scale = 1.0f + c->soft_rel;
+    k_splat<true><<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
+                                               c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
+                                               ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
+                                               c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
+                                               ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(),
+                                               ws.soft_acc.as<unsigned long long>(), scale);
 }
 
 void launch_clear_keys(Workspace& ws, cudaStream_t st) {
@@ -550,7 +598,8 @@ void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
     dim3 g((ws.W + 63) / 64, (ws.H + 63) / 64, ws.B);
     k_resolve_pyramid<<<g, 256, 0, st>>>(ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(), ws.W, ws.H,
                                          ws.nlev, ws.depth.as<float>(), ws.rgba.as<uint32_t>(), ws.pyr_m.as<float>(),
-                                         pyramid_floats(ws.W, ws.H, ws.nlev));
+                                         pyramid_floats(ws.W, ws.H, ws.nlev),
+                                         c->soft_rel > 0.0f ? ws.soft_acc.as<unsigned long long>() : nullptr);
 }
 
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int kind, bool write_u0,

@@ -151,7 +151,7 @@ struct Server {
 };
 
 static size_t request_bytes(const lnr_ctx* c, int B, int W, int H, lnr_precision p) {
-    return unet_act_bytes(c->unet, B, W, H, p) + frame_bytes(B, W, H);
+    return unet_act_bytes(c->unet, B, W, H, p) + frame_bytes(B, W, H, c->soft_rel > 0.0f);
 }
 
 bool Server::launch(Slot& s, std::vector<uint64_t>& batch) {
