@@ -230,6 +230,24 @@ def num_threads():
     return int(lib().orc_num_threads())
 
 
+def training_input(D, U0, rgb, gt, zfar, unfiltered=False):
+    """Network input (H, W, 5) FP32 of one synthetic training pair (Sec. 3, "Training Data
+    Generation"): the projection's depth D and alpha A^s (the filter's kept mask, U0 finite)
+    with the ground-truth photo gt zeroed where A^s = 0.  The unfiltered variant keeps every
+    filled pixel (D finite): foreground (kept) pixels take gt, background (dropped) pixels
+    the projected colour rgb / 255.  D channel z / zfar; zero where the pixel is not used."""
+    D = np.asarray(D, np.float32)
+    fg = np.isfinite(np.asarray(U0, np.float32))
+    used = (fg | np.isfinite(D)) if unfiltered else fg
+    out = np.zeros(D.shape + (5,), np.float32)
+    col = np.where(fg[..., None], np.asarray(gt, np.float32),
+                   np.asarray(rgb, np.uint8).astype(np.float32) / np.float32(255.0))
+    out[..., :3] = np.where(used[..., None], col, np.float32(0.0))
+    out[..., 3] = np.where(used, D / np.float32(zfar), np.float32(0.0))
+    out[..., 4] = used.astype(np.float32)
+    return out
+
+
 def render(grid: Grid, view, intr, W, H, n_levels, fs, weights=None, ch=None, has_bn=False,
            brute=False, soft=0.0):
     """Every stage of one frame: keys, RGBDA before the filter, kept depth, U-Net input

@@ -244,6 +244,26 @@ def test_soft_wide_threshold_is_mean_of_the_pixel():
     assert checked > 100
 
 
+def test_training_input_hand_case():
+    """Training-pair input (Sec. 3, "Training Data Generation") on four hand-built pixels:
+    kept (foreground), filled but dropped (background), empty, kept."""
+    inf = np.float32(np.inf)
+    D = np.array([[2.0, 4.0], [inf, 10.0]], np.float32)
+    U0 = np.array([[2.0, inf], [inf, 10.0]], np.float32)
+    rgb = np.array([[[255, 0, 51], [102, 255, 0]], [[0, 0, 0], [1, 2, 3]]], np.uint8)
+    gt = np.array([[[0.1, 0.2, 0.3], [0.4, 0.5, 0.6]], [[0.7, 0.8, 0.9], [1.0, 0.0, 0.5]]], np.float32)
+    f = oracle.training_input(D, U0, rgb, gt, 100.0)
+    u = oracle.training_input(D, U0, rgb, gt, 100.0, unfiltered=True)
+    g32 = lambda *v: np.array(v, np.float32)
+    assert np.array_equal(f[0, 0], g32(0.1, 0.2, 0.3, 0.02, 1.0))     # foreground: gt, z / zfar
+    assert np.array_equal(f[0, 1], g32(0, 0, 0, 0, 0))                 # dropped: zero alpha
+    assert np.array_equal(f[1, 0], g32(0, 0, 0, 0, 0))                 # empty
+    assert np.array_equal(f[1, 1], g32(1.0, 0.0, 0.5, 0.1, 1.0))
+    assert np.array_equal(u[0, 0], f[0, 0]) and np.array_equal(u[1, 1], f[1, 1])
+    assert np.array_equal(u[0, 1], g32(0.4, 1.0, 0.0, 0.04, 1.0))      # background: point colour
+    assert np.array_equal(u[1, 0], g32(0, 0, 0, 0, 0))
+
+
 def test_georeferencing_offset_is_bit_exact():
     """Translating cloud and camera by a large exact offset leaves every key unchanged."""
     s = synth.room_scene(n_points=30000, seed=4)
