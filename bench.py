@@ -220,6 +220,61 @@ def run_accuracy(args, scene, views, weights, lnr, synth):
     r.close()
 
 
+def run_sweep(args, lnr, synth):
+    """Density / size sweep (the paper's output-sensitivity claim, Sec. 1, and its results figure's 10%
+    decimation): the multiroom_20M scan decimated to 10..100% (seeded subset) and the
+    100M-point scan, each rendered as 8 x 1080p views per step in BF16.  Per configuration:
+    points, visible points per view, raster and U-Net milliseconds per step (library stage
+    events), frames/s and visible points/s."""
+    from synth.workloads import MULTIROOM_20M, MULTIROOM_100M, make_scene
+    weights = synth.unet_weights(CH, seed=1)
+    intr = synth.intrinsics_for(W, H)
+    B = 8
+    out = []
+
+    def one(name, xyz, rgb, scan, views):
+        r = lnr.Renderer(0)
+        try:
+            r.load_cloud(xyz, rgb, scan)
+            r.build_grid(CELL)
+            r.set_unet(CH, weights, "bf16")
+            r.autotune(W, H, B)
+            vis = [int(r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1]) for v in views[:B]]
+            fs = [FS[k % 2] for k in range(B)]
+            for i in range(3):
+                r.render_batch(views[:B], intr, W, H, NLEV, fs)
+            r.set_timing(True)
+            tims = []
+            for i in range(5):
+                r.render_batch([views[(i + k) % len(views)] for k in range(B)], intr, W, H, NLEV, fs)
+                tims.append(r.get_timing())
+            r.set_timing(False)
+            med = lambda k: float(np.median([t[k] for t in tims]))
+            raster = med("cull") + med("splat") + med("resolve_pyramid") + med("upsample_pack")
+            frame = med("frame")
+            nvis = float(np.mean(vis))
+            out.append({"config": name, "n_points": int(len(xyz)), "visible_points_per_view": nvis,
+                        "raster_ms_per_step": raster, "splat_ms_per_step": med("splat"),
+                        "unet_ms_per_step": med("unet"), "frame_ms_per_step": frame,
+                        "frames_per_s": B / (frame * 1e-3),
+                        "visible_points_per_s": nvis * B / (raster * 1e-3)})
+        finally:
+            r.close()
+
+    s20 = make_scene(MULTIROOM_20M, device="cuda")
+    views = synth.random_poses(s20, N_POSES, seed=2)
+    rng = np.random.default_rng(0)
+    order = rng.permutation(len(s20.xyz))
+    for frac in (0.1, 0.25, 0.5, 1.0):
+        keep = np.sort(order[:int(frac * len(order))])
+        one(f"multiroom_20M at {int(frac * 100)}%", s20.xyz[keep], s20.rgb[keep], s20.scan_id[keep], views)
+    del s20
+    s100 = make_scene(MULTIROOM_100M, device="cuda")
+    one("multiroom_100M", s100.xyz, s100.rgb, s100.scan_id, synth.random_poses(s100, N_POSES, seed=2))
+    print(json.dumps({"sweep": out, "W": W, "H": H, "views_per_step": B, "precision": "bf16",
+                      "n_levels": NLEV, "cell": CELL}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,6 +286,9 @@ def main():
     ap.add_argument("--accuracy", type=int, default=0, metavar="VIEWS",
                     help="report max abs error and PSNR of the FP32 / BF16 / FP8 U-Nets against the "
                          "oracle's FP64 U-Net on VIEWS 1080p views (slow: the oracle runs on the host)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="density / size sweep (decimated 20M scan, 100M scan): raster and U-Net "
+                         "time, frames/s and visible points/s per configuration")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched path only (no stage timing, plain, serving or CPU legs): "
                          "the command the ncu captures in profiles/ run")
@@ -252,6 +310,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    if args.sweep:
+        return run_sweep(args, lnr, synth)
     scene, views, weights = make_workload(dev)
     if args.accuracy:
         return run_accuracy(args, scene, views, weights, lnr, synth)

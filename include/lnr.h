@@ -113,6 +113,20 @@ lnr_status lnr_set_unet(lnr_ctx* ctx, const lnr_unet_desc* desc, const float* we
  * LNR_E_STATE until the net is calibrated. */
 lnr_status lnr_set_precision(lnr_ctx* ctx, lnr_precision precision);
 
+/* Network input of one synthetic training pair (Sec. 3, "Training Data Generation").  The frame is
+ * projected and filtered at this view exactly as lnr_render does (n_levels, fs), then
+ * composed with a caller's ground-truth photo gt_rgb (host, H*W*3 FP32 HWC, any range):
+ *  - unfiltered = 0 (the filtered net's input): RGB = gt where the filter keeps the
+ *    pixel (A^s = 1), D = z / zfar there, A = A^s; zero elsewhere;
+ *  - unfiltered = 1 (the unfiltered net's input): every filled pixel, RGB = gt for pixels
+ *    the filter keeps (foreground) and the projected point colour / 255 for pixels it
+ *    drops (background), D = z / zfar, A = 1; zero where no point falls.
+ * out: host, H*W*5 FP32 (r, g, b, D, A).  The ground truth of the pair is gt itself.
+ * Errors as lnr_render_stage; LNR_E_ARG for null gt_rgb / out.  Allocates temporaries. */
+lnr_status lnr_training_input(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr,
+                              int W, int H, int n_levels, float fs, const float* gt_rgb,
+                              int unfiltered, float* out);
+
 /* Collision rule of the splat (Sec. 3, "Point Cloud Projection").  rel = 0 (the default):
  * hard z-buffer, each pixel keeps its nearest point (depth ties: lower sorted position).
  * rel > 0: soft z-buffer, the pixel's colour is the per-channel integer mean, rounded half

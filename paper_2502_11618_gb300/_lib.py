@@ -25,7 +25,8 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
-           "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer"]
+           "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer",
+           "lnr_training_input"]
 
 
 class LnrError(RuntimeError):
@@ -71,6 +72,7 @@ def lib():
             "lnr_set_unet": ([p, C.POINTER(UnetDesc), p, sz, i], st),
             "lnr_set_precision": ([p, i], st),
             "lnr_set_soft_zbuffer": ([p, f], st),
+            "lnr_training_input": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, i, p], st),
             "lnr_render": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, i], st),
             "lnr_render_stage": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, i, p, i], st),
             "lnr_render_batch": ([p, i, p, p, i, i, i, p, p, i], st),
@@ -187,6 +189,18 @@ class Renderer:
         """0: hard z-buffer (default); rel > 0: soft z-buffer averaging the colours of the
         points within z_front * (1 + rel) of each pixel's front."""
         self._check(self._L.lnr_set_soft_zbuffer(self._c, float(rel)))
+
+    def training_input(self, view, intr, W, H, n_levels, fs, gt_rgb, unfiltered=False):
+        """(H, W, 5) FP32 network input of a synthetic training pair built from the
+        ground-truth image gt_rgb (H, W, 3) at this view; see lnr_training_input."""
+        gt = np.ascontiguousarray(gt_rgb, dtype=np.float32)
+        if gt.shape != (H, W, 3):
+            raise ValueError("gt_rgb must be (H, W, 3)")
+        out = np.empty((H, W, 5), np.float32)
+        self._check(self._L.lnr_training_input(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)),
+                                               W, H, n_levels, float(fs), _ptr(gt), int(bool(unfiltered)),
+                                               _ptr(out)))
+        return out
 
     def set_precision(self, precision):
         self._check(self._L.lnr_set_precision(self._c, PRECISIONS.get(precision, precision)))

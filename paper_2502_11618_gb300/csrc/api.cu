@@ -539,6 +539,34 @@ lnr_status lnr_render(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in
     return lnr_render_batch(c, 1, view, in, W, H, nlev, &fs, out, on_device);
 }
 
+lnr_status lnr_training_input(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev,
+                              float fs, const float* gt_rgb, int unfiltered, float* out) {
+    if (!c) return LNR_E_ARG;
+    lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, false);
+    if (s != LNR_OK) return s;
+    if (!gt_rgb || !out) return fail(c, LNR_E_ARG, "null ground truth or output");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    if (s != LNR_OK) return s;
+    enqueue_frame(c, ws, ws.stream, LNR_STAGE_FILTERED, c->prec, false);
+    const size_t P = (size_t)W * H;
+    DBuf gt, o5;
+    cudaError_t e = gt.ensure(12 * P);
+    if (!e) e = o5.ensure(20 * P);
+    if (!e) e = cudaMemcpyAsync(gt.p, gt_rgb, 12 * P, cudaMemcpyHostToDevice, ws.stream);
+    if (!e) {
+        launch_training_input(ws, gt.as<float>(), in->zfar, unfiltered != 0, o5.as<float>(), ws.stream);
+        e = cudaMemcpyAsync(out, o5.p, 20 * P, cudaMemcpyDeviceToHost, ws.stream);
+    }
+    if (!e) e = cudaStreamSynchronize(ws.stream);
+    if (!e) e = cudaGetLastError();
+    gt.release();
+    o5.release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "training_input");
+    return LNR_OK;
+}
+
 lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev,
                             float fs, int stage, void* out, int on_device) {
     if (!c) return LNR_E_ARG;

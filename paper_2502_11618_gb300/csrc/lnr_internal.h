@@ -204,6 +204,8 @@ void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_clear_keys(Workspace& ws, cudaStream_t st);
 void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,
+                           cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
 // unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC16, 2 = none (stage taps only).
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,

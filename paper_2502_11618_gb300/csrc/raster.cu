@@ -634,6 +634,48 @@ void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int 
     k_upsample<<<g, 256, 0, st>>>(a);
 }
 
+// Network input of one synthetic training pair (Sec. 3, "Training Data Generation"): per pixel from the
+// raw depth / colour of the projection, the kept depth of the filter and the ground-truth
+// image gt (FP32 RGB).  filtered input: (gt * A^s, z / zfar, A^s) with A^s the kept mask;
+// unfiltered input: every filled pixel, kept ones (foreground) with gt, filtered-out ones
+// (background) with the projected colour / 255, D = z / zfar, A = 1; zero elsewhere.
+__global__ void k_training_input(const float* __restrict__ depth, const uint32_t* __restrict__ rgba,
+                                 const float* __restrict__ kept, const float* __restrict__ gt, float zfar,
+                                 int unfiltered, int64_t npx, float* __restrict__ out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npx; q += (int64_t)gridDim.x * blockDim.x) {
+        const float z = depth[q], zk = kept[q];
+        const bool filled = z != INFINITY, fg = zk != INFINITY;
+        float r = 0.f, g = 0.f, b = 0.f, d = 0.f, a = 0.f;
+        if (fg || (unfiltered && filled)) {
+            if (fg) {
+                r = gt[3 * q];
+                g = gt[3 * q + 1];
+                b = gt[3 * q + 2];
+            } else {
+                const uint32_t c = rgba[q];
+                r = __fdiv_rn((float)(c & 255u), 255.0f);
+                g = __fdiv_rn((float)((c >> 8) & 255u), 255.0f);
+                b = __fdiv_rn((float)((c >> 16) & 255u), 255.0f);
+            }
+            d = __fdiv_rn(z, zfar);
+            a = 1.0f;
+        }
+        float* o = out + 5 * q;
+        o[0] = r;
+        o[1] = g;
+        o[2] = b;
+        o[3] = d;
+        o[4] = a;
+    }
+}
+
+void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,
+                           cudaStream_t st) {
+    const int64_t npx = (int64_t)ws.W * ws.H;
+    k_training_input<<<(unsigned)std::min<int64_t>((npx + 255) / 256, 8192), 256, 0, st>>>(
+        ws.depth.as<float>(), ws.rgba.as<uint32_t>(), ws.u0.as<float>(), gt, zfar, unfiltered, npx, out);
+}
+
 void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t npx, cudaStream_t st) {
     k_extract5<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(unet_in, kind, out5, npx);
 }
