@@ -27,7 +27,7 @@ lnr_status cuda_fail(lnr_ctx* c, cudaError_t e, const char* where) {
 }
 
 void Workspace::release() {
-    DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_cell, &vis_pref, &vis_tot, &keys,
+    DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_cell, &vis_pref, &vis_tot, &chunk_cell, &keys,
                    &soft_acc, &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
     for (DBuf* b : all) b->release();
     for (auto& a : act) a.release();
@@ -103,14 +103,15 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
     cudaError_t e;
     const void* before[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
                             ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
-                            ws.soft_acc.p};
+                            ws.soft_acc.p, ws.chunk_cell.p};
     const size_t P = (size_t)W * H;
     const int nb = cull_blocks(c->ncells);
     const size_t pf = pyramid_floats(W, H, kMaxLevels);
     if ((e = ws.view.ensure(sizeof(ViewDev) * B)) || (e = ws.cull_flag.ensure(4 * c->ncells * B)) ||
         (e = ws.cull_cnt.ensure(4 * c->ncells * B)) || (e = ws.cull_bsum.ensure(8 * (size_t)nb * B)) ||
         (e = ws.vis_cell.ensure(4 * c->ncells * B)) || (e = ws.vis_pref.ensure(4 * c->ncells * B)) ||
-        (e = ws.vis_tot.ensure(8 * B)) || (e = ws.depth.ensure(4 * P * B)) || (e = ws.rgba.ensure(4 * P * B)) ||
+        (e = ws.vis_tot.ensure(8 * B)) || (e = ws.chunk_cell.ensure(4 * splat_max_chunks(c->n) * B)) ||
+        (e = ws.depth.ensure(4 * P * B)) || (e = ws.rgba.ensure(4 * P * B)) ||
         (e = ws.pyr_m.ensure(4 * pf * B)) || (e = ws.pyr_u.ensure(4 * pf * B)) || (e = ws.u0.ensure(4 * P * B)) ||
         (e = ws.out.ensure(12 * P * B)))
         return e;
@@ -132,7 +133,7 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
             if ((e = cudaEventCreate(&ev))) return e;
     const void* after[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
                            ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
-                           ws.soft_acc.p};
+                           ws.soft_acc.p, ws.chunk_cell.p};
     for (size_t i = 0; i < sizeof(before) / sizeof(before[0]); ++i)
         if (before[i] != after[i]) ws.alloc_gen++;
     ws.B = B;

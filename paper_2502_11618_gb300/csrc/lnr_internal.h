@@ -117,6 +117,7 @@ struct Workspace {
     DBuf view;                              // ViewDev[B]
     DBuf cull_flag, cull_cnt, cull_bsum;    // per-cell temporaries
     DBuf vis_cell, vis_pref, vis_tot;       // compacted visible cells, point prefix, totals
+    DBuf chunk_cell;                        // per view: first visible cell of every splat chunk
     DBuf keys;                              // uint64 [B][P]
     bool keys_dirty = true;
     DBuf soft_acc;                          // soft z-buffer sums, uint64 [B][P][2] (soft mode only)
@@ -204,6 +205,7 @@ void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_clear_keys(Workspace& ws, cudaStream_t st);
 void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+size_t splat_max_chunks(uint64_t npoints);  // entries per view of the splat's chunk -> first cell table
 void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,
                            cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.

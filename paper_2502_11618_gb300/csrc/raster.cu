@@ -180,10 +180,14 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_scan(uint32_t* __restrict
 }
 
 // Phase 3: compaction.  vis_cell[view][r] = cell id, vis_pref[view][r] = visible points
-// before it.
+// before it, and chunk_cell[view][k] = r for every splat chunk k (kSplatChunk visible
+// points) whose first point lies in this cell, so that the splat finds a chunk's cells
+// without searching.
 __global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ cnt,
                                const uint32_t* __restrict__ bsum, int nb, int64_t C,
-                               uint32_t* __restrict__ vis_cell, uint32_t* __restrict__ vis_pref) {
+                               const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ vis_cell,
+                               uint32_t* __restrict__ vis_pref, uint32_t* __restrict__ chunk_cell,
+                               size_t max_chunks) {
     const int view = blockIdx.y;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
@@ -192,17 +196,19 @@ __global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t
     int b = (int)(c / kCullTile);
     const uint32_t* bs = bsum + ((size_t)view * nb + b) * 2;
     uint32_t r = bs[0] + f;
+    const uint32_t pref = bs[1] + cnt[(size_t)view * C + c];
     vis_cell[(size_t)view * C + r] = (uint32_t)c;
-    vis_pref[(size_t)view * C + r] = bs[1] + cnt[(size_t)view * C + c];
+    vis_pref[(size_t)view * C + r] = pref;
+    const uint32_t n = cell_start[c + 1] - cell_start[c];  // > 0: only non-empty cells are visible
+    uint32_t* cc = chunk_cell + (size_t)view * max_chunks;
+    for (uint32_t k = (pref + kSplatChunk - 1) / kSplatChunk; k <= (pref + n - 1) / kSplatChunk; ++k) cc[k] = r;
 }
 
 // ------------------------------------------------------------------ splat ----
 
-struct __align__(16) ChunkCell {
-    float o[3];      // camera-space origin of the cell
-    uint32_t pref;   // visible points before the cell
-    uint32_t base;   // sorted position of its first point minus pref (mod 2^32)
-};
+// Splat loads in flight per thread: kSplatBatch points' offsets are fetched before any of
+// them is projected (the pass is bound by load latency, not bandwidth).
+constexpr int kSplatBatch = 4;
 
 // SOFT = false: hard z-buffer pass, atomicMin of (bits(z) << 32 | position) per pixel.
 // SOFT = true: second pass of the soft z-buffer (Sec. 3: colours of points arriving at
@@ -211,14 +217,18 @@ struct __align__(16) ChunkCell {
 // count to the pixel's integer sums -- acc[2q] = r << 32 | g, acc[2q+1] = b << 32 | n --
 // so the result does not depend on the order of the atomics.
 template <bool SOFT>
-__global__ void __launch_bounds__(kSplatThreads) k_splat(
+__global__ void __launch_bounds__(kSplatThreads, 4) k_splat(
     const ViewDev* __restrict__ views, const uint32_t* __restrict__ cell_start, int dx, int dy,
     int64_t C, const uint32_t* __restrict__ vis_cell, const uint32_t* __restrict__ vis_pref,
     const uint32_t* __restrict__ tot, const float* __restrict__ ox, const float* __restrict__ oy,
     const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys,
-    const uint32_t* __restrict__ rgbs, unsigned long long* __restrict__ acc, float scale) {
-    __shared__ ChunkCell cells[kSplatChunk];
-    __shared__ int s_vc0, s_nc;
+    const uint32_t* __restrict__ rgbs, unsigned long long* __restrict__ acc, float scale,
+    const uint32_t* __restrict__ chunk_cell, size_t max_chunks) {
+    // per chunk cell: camera-space origin + (sorted position of its first point - pref),
+    // and pref = visible points before it (a separate array: 20 KB + 8 KB keeps five
+    // blocks per SM)
+    __shared__ float4 cells[kSplatChunk];
+    __shared__ uint32_t cpref[kSplatChunk];
     const int view = blockIdx.y;
     const ViewDev v = views[view];
     const uint32_t nvc = tot[2 * view], npts = tot[2 * view + 1];
@@ -230,69 +240,77 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
         uint64_t start = chunk * kSplatChunk;
         if (start >= npts) break;
         uint32_t end = (uint32_t)(start + kSplatChunk < (uint64_t)npts ? start + kSplatChunk : (uint64_t)npts);
-        if (threadIdx.x == 0) {
-            // last visible cell with pref <= start, and last with pref < end
-            uint32_t lo = 0, hi = nvc - 1;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi + 1) >> 1;
-                if (vp[mid] <= (uint32_t)start) lo = mid; else hi = mid - 1;
-            }
-            uint32_t a = lo;
-            hi = nvc - 1;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi + 1) >> 1;
-                if (vp[mid] < end) lo = mid; else hi = mid - 1;
-            }
-            s_vc0 = (int)a;
-            s_nc = (int)(lo - a + 1);
+        // first cell: the one holding point `start`; last: the one holding point end - 1
+        const uint32_t* ck = chunk_cell + (size_t)view * max_chunks;
+        const int vc0 = (int)ck[chunk];
+        int vc1 = (int)nvc - 1;
+        if (end < npts) {
+            vc1 = (int)ck[chunk + 1];
+            if (vp[vc1] >= end) --vc1;
         }
-        __syncthreads();
-        const int vc0 = s_vc0, nc = s_nc;
+        const int nc = vc1 - vc0 + 1;
         for (int t = threadIdx.x; t < nc; t += kSplatThreads) {
             uint32_t c = vc[vc0 + t];
             int64_t i = c % (uint32_t)dx, j = (c / (uint32_t)dx) % (uint32_t)dy, k = c / ((uint32_t)dx * (uint32_t)dy);
-            ChunkCell cc;
-            cell_cam(i, j, k, v, cc.o);
-            cc.pref = vp[vc0 + t];
-            cc.base = cell_start[c] - cc.pref;
-            cells[t] = cc;
+            float o[3];
+            cell_cam(i, j, k, v, o);
+            const uint32_t pref = vp[vc0 + t];
+            cells[t] = make_float4(o[0], o[1], o[2], __uint_as_float(cell_start[c] - pref));
+            cpref[t] = pref;
         }
         __syncthreads();
         int cur = 0;
-        for (uint32_t e = (uint32_t)start + threadIdx.x; e < end; e += kSplatThreads) {
-            // the cell of element e: last chunk cell with pref <= e (elements increase)
-            int lo = cur, hi = nc - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (cells[mid].pref <= e) lo = mid; else hi = mid - 1;
-            }
-            cur = lo;
-            const ChunkCell& cc = cells[lo];
-            uint32_t pos = e + cc.base;
-            float px = ox[pos], py = oy[pos], pz = oz[pos];
-            float p[3];
+        for (uint32_t e0 = (uint32_t)start + threadIdx.x; e0 < end; e0 += kSplatBatch * kSplatThreads) {
+            float px[kSplatBatch], py[kSplatBatch], pz[kSplatBatch];
+            uint32_t pos[kSplatBatch];
+            int cell[kSplatBatch];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                float t = __fmaf_rn(v.Rf[3 * r + 2], pz, cc.o[r]);
-                t = __fmaf_rn(v.Rf[3 * r + 1], py, t);
-                p[r] = __fmaf_rn(v.Rf[3 * r + 0], px, t);
+            for (int b = 0; b < kSplatBatch; ++b) {
+                const uint32_t e = e0 + b * kSplatThreads;
+                cell[b] = -1;
+                if (e >= end) continue;
+                // the cell of element e: last chunk cell with pref <= e (elements increase)
+                int lo = cur, hi = nc - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (cpref[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                cur = lo;
+                cell[b] = lo;
+                pos[b] = e + __float_as_uint(cells[lo].w);
+                px[b] = ox[pos[b]];
+                py[b] = oy[pos[b]];
+                pz[b] = oz[pos[b]];
             }
-            const float z = p[2];
-            if (!(z > v.znear && z < v.zfar)) continue;
-            const float u = __fadd_rn(__fdiv_rn(__fmul_rn(v.fx, p[0]), z), v.cx);
-            const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
-            if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
-            const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
-            if (!SOFT) {
-                const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos;
-                atomicMin(&kv[pix], key);
-            } else {
-                const unsigned long long front = kv[pix];
-                if (front == kEmpty || !(z <= __fmul_rn(__uint_as_float((uint32_t)(front >> 32)), scale))) continue;
-                const uint32_t col = rgbs[pos];
-                unsigned long long* a = acc + 2 * ((size_t)view * W * H + pix);
-                atomicAdd(a, ((unsigned long long)(col & 255u) << 32) | ((col >> 8) & 255u));
-                atomicAdd(a + 1, ((unsigned long long)((col >> 16) & 255u) << 32) | 1ull);
+#pragma unroll
+            for (int b = 0; b < kSplatBatch; ++b) {
+                if (cell[b] < 0) continue;
+                const float4 co = cells[cell[b]];
+                const float cell_o[3] = {co.x, co.y, co.z};
+                float p[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    float t = __fmaf_rn(v.Rf[3 * r + 2], pz[b], cell_o[r]);
+                    t = __fmaf_rn(v.Rf[3 * r + 1], py[b], t);
+                    p[r] = __fmaf_rn(v.Rf[3 * r + 0], px[b], t);
+                }
+                const float z = p[2];
+                if (!(z > v.znear && z < v.zfar)) continue;
+                const float u = __fadd_rn(__fdiv_rn(__fmul_rn(v.fx, p[0]), z), v.cx);
+                const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
+                if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
+                const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
+                if (!SOFT) {
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos[b];
+                    atomicMin(&kv[pix], key);
+                } else {
+                    const unsigned long long front = kv[pix];
+                    if (front == kEmpty || !(z <= __fmul_rn(__uint_as_float((uint32_t)(front >> 32)), scale))) continue;
+                    const uint32_t col = rgbs[pos[b]];
+                    unsigned long long* a = acc + 2 * ((size_t)view * W * H + pix);
+                    atomicAdd(a, ((unsigned long long)(col & 255u) << 32) | ((col >> 8) & 255u));
+                    atomicAdd(a + 1, ((unsigned long long)((col >> 16) & 255u) << 32) | 1ull);
+                }
             }
         }
         __syncthreads();
@@ -532,6 +550,8 @@ __global__ void k_extract5(const void* in, int kind, float* out, int64_t npx) {
 
 }  // namespace
 
+size_t splat_max_chunks(uint64_t npoints) { return (size_t)(npoints / kSplatChunk) + 2; }
+
 int cull_blocks(int64_t ncells) { return (int)((ncells + kCullTile - 1) / kCullTile); }
 
 void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
@@ -544,8 +564,9 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
     k_cull_scan<<<ws.B, kCullThreads, 0, st>>>(ws.cull_bsum.as<uint32_t>(), nb, ws.vis_tot.as<uint32_t>());
     dim3 g3((unsigned)((c->ncells + 255) / 256), ws.B);
     k_cull_compact<<<g3, 256, 0, st>>>(ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
-                                       ws.cull_bsum.as<uint32_t>(), nb, c->ncells, ws.vis_cell.as<uint32_t>(),
-                                       ws.vis_pref.as<uint32_t>());
+                                       ws.cull_bsum.as<uint32_t>(), nb, c->ncells, c->cell_start.as<uint32_t>(),
+                                       ws.vis_cell.as<uint32_t>(), ws.vis_pref.as<uint32_t>(),
+                                       ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
 }
 
 void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
@@ -555,7 +576,8 @@ void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                                 c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
                                                 ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
                                                 c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
-                                                ws.keys.as<unsigned long long>(), nullptr, nullptr, 1.0f);
+                                                ws.keys.as<unsigned long long>(), nullptr, nullptr, 1.0f,
+                                                ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
 }
 
 // Second pass of the soft z-buffer (after launch_splat has finished the keys).
@@ -572,7 +594,8 @@ void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                                ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
                                                c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
                                                ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(),
-                                               ws.soft_acc.as<unsigned long long>(), scale);
+                                               ws.soft_acc.as<unsigned long long>(), scale,
+                                               ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
 }
 
 void launch_clear_keys(Workspace& ws, cudaStream_t st) {
