@@ -457,6 +457,15 @@ struct HParams {
     float* head_out;
     int head_o;
     int* err;
+    // TMA-store epilogue (ostage = 1): per epilogue warp a staging area of ost_warp bytes at
+    // ost_off from the 1024-aligned base: (pool ? 2 : 1) rows of 32 pixels x N channels,
+    // then (pool) 16 pooled pixels, every part 1024-aligned; rows split into boxes of
+    // orow_b bytes (<= 128, swizzle mask omask), pooled rows into prow_b (pmask)
+    CUtensorMap omap;    // output: 4-D {N, W, H, B} box {orow_b/e, 32, 1, 1}; parity: 5-D {N, 2, W/2, H, B}
+    CUtensorMap pmap;    // pooled output: 4-D {N, W/2, H/2, B} box {prow_b/e, 16, 1, 1}
+    int ostage;
+    uint32_t ost_off, ost_warp, ost_row, ost_pool;  // staging offset, bytes per warp, per row part, pool part offset
+    uint32_t orow_b, omask, prow_b, pmask;
 };
 
 __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2) {
@@ -487,6 +496,49 @@ __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
     reinterpret_cast<uint4*>(dst)[0] = pk[0];
     reinterpret_cast<uint4*>(dst)[1] = pk[1];
 }
+
+// 16 channels packed for a 16-byte-chunk store: BF16 (two chunks) or E4M3 of v * inv (one).
+__device__ __forceinline__ void pack_bf16x16(const float* v, uint4 (&pk)[2]) {
+    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        pw[j] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+}
+__device__ __forceinline__ uint4 pack_fp8x16(const float* v, float inv) {
+    uint4 pk;
+    uint16_t* ph = reinterpret_cast<uint16_t*>(&pk);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        ph[j] = __nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * inv, v[2 * j + 1] * inv), __NV_SATFINITE, __NV_E4M3);
+    return pk;
+}
+
+// Epilogue staging for TMA stores: 16 bytes at byte `off` of a 1024-aligned staging box
+// whose rows are swizzled like TMA's 32/64/128-byte modes (16-byte chunk index XOR address
+// bits 7-9, `mask` = 1, 3 or 7), so that a warp writing one row per lane hits distinct banks.
+__device__ __forceinline__ void sts_swz(uint32_t buf, uint32_t off, uint4 v, uint32_t mask) {
+    const uint32_t a = buf + off;
+    const uint32_t ph = a ^ (((a >> 7) & mask) << 4);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ph), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, uint32_t src, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"((uint64_t)m),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* m, uint32_t src, int c0, int c1, int c2, int c3, int c4) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"((uint64_t)m),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed store has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // 16 TMEM columns of this warp's lanes into r without waiting; tmem_wait16 completes it.
 __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
@@ -665,7 +717,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* const gbase = smem_raw + (base - raw);
     const int S = p.stages;
-    const uint32_t bars = base + S * p.stage_bytes;
+    const uint32_t stg = base + S * p.stage_bytes;  // epilogue staging (TMA stores), 1024-aligned
+    const uint32_t bars = stg + (p.ostage ? kEpiWarps * p.ost_warp : 0u);
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (S + s); };
     auto tfull = [&](int b) { return bars + 8u * (2 * S + b); };
@@ -852,6 +905,10 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                 for (int r = 2 * eh; r < R; r += 4) {
                     const int x = x0 + m, y = y0 + r;
                     const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
+                    if (p.ostage) {  // the staging of the previous row pair has been read
+                        if (lane == 0) bulk_wait_read();
+                        __syncwarp();
+                    }
                     for (int c0 = 0; c0 < N; c0 += 16) {
                         uint32_t u0[16], u1[16];
                         tmem_ld16_async(trow + (uint32_t)(r * N + c0), u0);
@@ -866,6 +923,46 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                             const float a = fmaxf(f0[j], f1[j]);
                             pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                         }
+                        if (p.ostage) {
+                            const uint32_t eo = p.out_fp8 ? 1u : 2u, epb = p.pool_fp8 ? 1u : 2u;
+                            auto stage_row = [&](uint32_t buf, const float* f) {
+                                if (p.out_fp8) {
+                                    const uint32_t cb = (uint32_t)c0 * eo;
+                                    sts_swz(buf, (cb / p.orow_b) * 32u * p.orow_b + (uint32_t)lane * p.orow_b + cb % p.orow_b,
+                                            pack_fp8x16(f, p.inv_out), p.omask);
+                                } else {
+                                    uint4 pk[2];
+                                    pack_bf16x16(f, pk);
+#pragma unroll
+                                    for (int h2 = 0; h2 < 2; ++h2) {
+                                        const uint32_t cb = (uint32_t)(c0 + 8 * h2) * eo;
+                                        sts_swz(buf, (cb / p.orow_b) * 32u * p.orow_b + (uint32_t)lane * p.orow_b + cb % p.orow_b,
+                                                pk[h2], p.omask);
+                                    }
+                                }
+                            };
+                            const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
+                            stage_row(wb, f0);
+                            stage_row(wb + p.ost_row, f1);
+                            if ((m & 1) == 0) {
+                                const uint32_t pb = wb + p.ost_pool, i = (uint32_t)lane >> 1;
+                                if (p.pool_fp8) {
+                                    const uint32_t cb = (uint32_t)c0;
+                                    sts_swz(pb, (cb / p.prow_b) * 16u * p.prow_b + i * p.prow_b + cb % p.prow_b,
+                                            pack_fp8x16(pm, p.inv_out), p.pmask);
+                                } else {
+                                    uint4 pk[2];
+                                    pack_bf16x16(pm, pk);
+#pragma unroll
+                                    for (int h2 = 0; h2 < 2; ++h2) {
+                                        const uint32_t cb = (uint32_t)(c0 + 8 * h2) * epb;
+                                        sts_swz(pb, (cb / p.prow_b) * 16u * p.prow_b + i * p.prow_b + cb % p.prow_b, pk[h2],
+                                                p.pmask);
+                                    }
+                                }
+                            }
+                            continue;
+                        }
                         const size_t e0 = (((size_t)n * p.H + y) * p.W + x) * N + c0;
                         const size_t e1 = e0 + (size_t)p.W * N;
                         const size_t ep = (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N + c0;
@@ -879,6 +976,24 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         if ((m & 1) == 0 && v1) {
                             if (p.pool_fp8) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + ep, pm, p.inv_out);
                             else st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
+                        }
+                    }
+                    if (p.ostage) {  // both rows and the pooled row leave by TMA (clipped at the image edges)
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
+                            const uint32_t eo = p.out_fp8 ? 1u : 2u, epb = p.pool_fp8 ? 1u : 2u;
+                            const int X = x0 + 32 * q;
+                            for (uint32_t sb = 0; sb * p.orow_b < (uint32_t)N * eo; ++sb) {
+                                const int ch = (int)(sb * p.orow_b / eo);
+                                tma_store_4d(&p.omap, wb + sb * 32u * p.orow_b, ch, X, y, n);
+                                tma_store_4d(&p.omap, wb + p.ost_row + sb * 32u * p.orow_b, ch, X, y + 1, n);
+                            }
+                            for (uint32_t sb = 0; sb * p.prow_b < (uint32_t)N * epb; ++sb)
+                                tma_store_4d(&p.pmap, wb + p.ost_pool + sb * 16u * p.prow_b, (int)(sb * p.prow_b / epb), X >> 1,
+                                             y >> 1, n);
+                            bulk_commit();
                         }
                     }
                 }
@@ -902,6 +1017,11 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     }
                     const size_t pix = ((size_t)n * p.H + y) * p.W + x;
                     float h[4] = {0.f, 0.f, 0.f, 0.f};
+                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
+                    if (p.ostage) {  // the staging of the previous row has been read
+                        if (lane == 0) bulk_wait_read();
+                        __syncwarp();
+                    }
                     for (int c0 = 0; c0 < N; c0 += 32) {
                         uint32_t u0[16], u1[16];
                         const bool two = c0 + 16 < N;
@@ -912,7 +1032,27 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         float f0[16], f1[16];
                         act16(u0, c0, f0);
                         if (two) act16(u1, c0 + 16, f1);
-                        if (p.head_out) {
+                        if (p.ostage) {
+                            const uint32_t eo = p.out_fp8 ? 1u : 2u;
+                            for (int hf = 0; hf < (two ? 2 : 1); ++hf) {
+                                const float* f = hf ? f1 : f0;
+                                const int cf = c0 + 16 * hf;
+                                if (p.out_fp8) {
+                                    const uint32_t cb = (uint32_t)cf;
+                                    sts_swz(wb, (cb / p.orow_b) * 32u * p.orow_b + (uint32_t)lane * p.orow_b + cb % p.orow_b,
+                                            pack_fp8x16(f, p.inv_out), p.omask);
+                                } else {
+                                    uint4 pk[2];
+                                    pack_bf16x16(f, pk);
+#pragma unroll
+                                    for (int h2 = 0; h2 < 2; ++h2) {
+                                        const uint32_t cb = (uint32_t)(cf + 8 * h2) * eo;
+                                        sts_swz(wb, (cb / p.orow_b) * 32u * p.orow_b + (uint32_t)lane * p.orow_b + cb % p.orow_b,
+                                                pk[h2], p.omask);
+                                    }
+                                }
+                            }
+                        } else if (p.head_out) {
 #pragma unroll
                             for (int o = 0; o < 4; ++o) {  // 4 independent chains (zero weights past head_o)
                                 const float4* w4 = reinterpret_cast<const float4*>(shw + o * N + c0);
@@ -954,12 +1094,28 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                             p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[4 * N + o])));
                         }
                     }
+                    if (p.ostage) {  // the row leaves by TMA (clipped at the image edges)
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            const uint32_t eo = p.out_fp8 ? 1u : 2u;
+                            for (uint32_t sb = 0; sb * p.orow_b < (uint32_t)N * eo; ++sb) {
+                                const int ch = (int)(sb * p.orow_b / eo);
+                                if (PAR)  // x = 2 X + cx: the 5-D view {N, 2, W/2, H, B}
+                                    tma_store_5d(&p.omap, wb + sb * 32u * p.orow_b, ch, x & 1, x0 + 32 * q, y, n);
+                                else
+                                    tma_store_4d(&p.omap, wb + sb * 32u * p.orow_b, ch, x0 + 32 * q, y, n);
+                            }
+                            bulk_commit();
+                        }
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty(b));
         }
+        if (p.ostage && lane == 0) bulk_wait_all();  // no store may outlive the staging
         if (leader && *flag) atomicExch(p.err, 7);
     }
     __syncthreads();
@@ -1322,6 +1478,17 @@ void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
     ckmax = 16;
 }
 
+// Shared-memory staging of the TMA-store epilogue, bytes per epilogue warp: (pool ? 2 : 1)
+// rows of 32 pixels x N channels of eo bytes, then (pool) 16 pooled pixels of ep bytes, every
+// part 1024-aligned; 0 when the layout has no matching TMA swizzle (row bytes not a power of
+// two >= 32).
+static uint32_t halo_ostage_warp(int N, bool pool, uint32_t eo, uint32_t ep) {
+    auto pow2 = [](uint32_t v) { return v >= 32 && (v & (v - 1)) == 0; };
+    if (!pow2((uint32_t)N * eo) || (pool && !pow2((uint32_t)N * ep))) return 0;
+    const uint32_t row = align_up(32u * N * eo, 1024);
+    return (pool ? 2 : 1) * row + (pool ? align_up(16u * N * ep, 1024) : 0);
+}
+
 // Element encoding of one halo-kernel launch: BF16 or E4M3 operands, BF16 or E4M3 output.
 struct HaloTypes {
     bool in8 = false, out8 = false, pool8 = false;
@@ -1331,7 +1498,7 @@ struct HaloTypes {
 
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
-                  int P, int ckmax, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
+                  int P, int ckmax, int O, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
     const int esize = ty.in8 ? 1 : 2;
     if (ty.in8 && ckmax < 32) return false;
     const void* whp = ty.in8 ? L.wh8[ckmax == 32 ? 0 : ckmax == 64 ? 1 : 2] : L.wh[ck_index(ckmax)];
@@ -1413,7 +1580,51 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.ntiles = B * p.tiles_y * p.tiles_x;
     }
     p.stage_bytes = stage;
-    p.stages = std::min<int>(8, (int)((220u * 1024u) / p.stage_bytes));
+    // epilogue stores through staging + TMA (no fused head: its outputs are per-pixel floats)
+    uint32_t stg_total = 0;
+    if (O) {
+        if (head_out) return false;
+        const uint32_t eo = ty.out8 ? 1u : 2u, epb = ty.pool8 ? 1u : 2u;
+        p.ost_warp = halo_ostage_warp(N, pool_out != nullptr, eo, epb);
+        if (!p.ost_warp) return false;
+        p.ostage = 1;
+        p.ost_row = align_up(32u * N * eo, 1024);
+        p.ost_pool = (pool_out ? 2u : 1u) * p.ost_row;
+        p.orow_b = std::min<uint32_t>((uint32_t)N * eo, 128u);
+        p.prow_b = std::min<uint32_t>((uint32_t)N * epb, 128u);
+        p.omask = p.orow_b == 128 ? 7u : p.orow_b == 64 ? 3u : 1u;
+        p.pmask = p.prow_b == 128 ? 7u : p.prow_b == 64 ? 3u : 1u;
+        stg_total = kEpiWarps * p.ost_warp;
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        const CUtensorMapDataType odt = ty.out8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        const cuuint64_t ro = (cuuint64_t)N * eo;
+        if (P) {  // fine pixel x = 2 X + cx
+            cuuint64_t dims[5] = {(cuuint64_t)N, 2, (cuuint64_t)W / 2, (cuuint64_t)H, (cuuint64_t)B};
+            cuuint64_t str[4] = {ro, 2 * ro, (cuuint64_t)W * ro, (cuuint64_t)H * W * ro};
+            cuuint32_t box[5] = {p.orow_b / eo, 1, 32, 1, 1};
+            ok = ok && encode_tiled(&p.omap, odt, 5, out, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    swizzle_pitch(p.orow_b), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        } else {
+            cuuint64_t dims[4] = {(cuuint64_t)N, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+            cuuint64_t str[3] = {ro, (cuuint64_t)W * ro, (cuuint64_t)H * W * ro};
+            cuuint32_t box[4] = {p.orow_b / eo, 32, 1, 1};
+            ok = ok && encode_tiled(&p.omap, odt, 4, out, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    swizzle_pitch(p.orow_b), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        if (pool_out) {
+            const CUtensorMapDataType pdt = ty.pool8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+            const cuuint64_t rp = (cuuint64_t)N * epb, Wh = (cuuint64_t)(W >> 1), Hh = (cuuint64_t)(H >> 1);
+            cuuint64_t dims[4] = {(cuuint64_t)N, Wh, Hh, (cuuint64_t)B};
+            cuuint64_t str[3] = {rp, Wh * rp, Hh * Wh * rp};
+            cuuint32_t box[4] = {p.prow_b / epb, 16, 1, 1};
+            ok = ok && encode_tiled(&p.pmap, pdt, 4, pool_out, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    swizzle_pitch(p.prow_b), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+    }
+    p.stages = std::min<int>(8, (int)((220u * 1024u - stg_total) / p.stage_bytes));
     (void)halo_stage_bytes;
     if (p.stages < 2) return false;
     if (!ok) {
@@ -1438,7 +1649,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
-    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 +
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16 +
                         4 * (size_t)(2 * N + (head_out ? 4 * (N + 1) : 0));
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams)) {
@@ -1512,8 +1723,17 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
         if (cfg.mode == 0) {
             halo_default(L, R, P, CK);
             if (ty.in8) CK = std::max(32, CK);
+            // untuned: TMA-store epilogue where it fits next to two pipeline stages
+            static const bool no_tma_store = [] {
+                const char* e = getenv("LNR_CONV_TMA_STORE");
+                return e && !strcmp(e, "0");
+            }();
+            if (!no_tma_store &&
+                tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, 1, st, ty))
+                return;
         }
-        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, st, ty)) return;
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, cfg.O, st, ty))
+            return;
         if (fp8) {  // no fallback for FP8: record and skip
             g_host_err = 8;
             return;
@@ -1547,13 +1767,22 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 if (c0 == last_ck[0] && c1 == last_ck[1]) continue;
                 last_ck[0] = c0;
                 last_ck[1] = c1;
-                if (halo_stage_bytes(L, r, P, ck, esize) * 2 > 220u * 1024u) continue;
+                const uint32_t sb = halo_stage_bytes(L, r, P, ck, esize);
+                if (sb * 2 > 220u * 1024u) continue;
                 TcConfig c;
                 c.mode = 1;
                 c.R = r;
                 c.P = P;
                 c.CK = ck;
                 out.push_back(c);
+                // the same tile with the TMA-store epilogue, where its staging fits
+                const bool fp8 = prec == LNR_FP8;
+                const uint32_t eo = fp8 && !L.out_bf16 ? 1u : 2u, ep = fp8 && !L.pool_bf16 ? 1u : 2u;
+                const uint32_t wst = L.head ? 0u : halo_ostage_warp(N, L.pool, eo, ep);
+                if (wst && sb * 2 + kEpiWarps * wst <= 220u * 1024u) {
+                    c.O = 1;
+                    out.push_back(c);
+                }
             }
         }
     return out;

@@ -40,6 +40,7 @@ struct ViewDev {
 struct TcConfig {
     int mode = 0;
     int R = 0, P = 0, CK = 0;
+    int O = 0;  // halo kernel: 1 = epilogue stores through shared-memory staging and TMA
 };
 
 // One convolution as the GPU runs it.
