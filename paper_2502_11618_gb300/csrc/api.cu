@@ -267,8 +267,11 @@ static lnr_status finish_output(lnr_ctx* c, Workspace& ws, float* out, size_t nf
         if (e != cudaSuccess) return cuda_fail(c, e, "render");
     }
     if (c->timing) read_timing(c, ws);
-    if ((!on_device || c->timing) && c->prec != LNR_FP32 && tc_error_word())
-        return fail(c, LNR_E_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait ran out)");
+    if ((!on_device || c->timing) && c->prec != LNR_FP32) {
+        const int w = tc_error_word();
+        if (w >= 5 && w <= 7) return fail(c, LNR_E_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait ran out)");
+        if (w) return fail(c, LNR_E_CUDA, "a tensor-core convolution could not be launched (code " + std::to_string(w) + ")");
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
     return LNR_OK;

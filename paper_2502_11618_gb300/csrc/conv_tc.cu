@@ -464,7 +464,8 @@ struct HParams {
     CUtensorMap omap;    // output: 4-D {N, W, H, B} box {orow_b/e, 32, 1, 1}; parity: 5-D {N, 2, W/2, H, B}
     CUtensorMap pmap;    // pooled output: 4-D {N, W/2, H/2, B} box {prow_b/e, 16, 1, 1}
     int ostage;
-    uint32_t ost_off, ost_warp, ost_row, ost_pool;  // staging offset, bytes per warp, per row part, pool part offset
+    int ost_nbuf;                                   // staging buffers per warp (1 or 2, used in turn)
+    uint32_t ost_off, ost_warp, ost_unit, ost_row, ost_pool;  // offset, bytes per warp, per buffer, row part, pool part
     uint32_t orow_b, omask, prow_b, pmask;
 };
 
@@ -537,6 +538,8 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap* m, uint32_t src,
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // every committed store has finished reading its shared-memory source
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all but the most recent committed store have finished reading their sources
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // every committed store is complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -889,6 +892,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
             }
         };
         int tcount = 0;
+        int oc = 0;  // rows (row pairs) this warp has staged: selects the staging buffer
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
             const int b = tcount & 1;
             if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
@@ -905,8 +909,13 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                 for (int r = 2 * eh; r < R; r += 4) {
                     const int x = x0 + m, y = y0 + r;
                     const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
-                    if (p.ostage) {  // the staging of the previous row pair has been read
-                        if (lane == 0) bulk_wait_read();
+                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp +
+                                        (uint32_t)(oc % p.ost_nbuf) * p.ost_unit;
+                    if (p.ostage) {  // the store that last used this staging buffer has read it
+                        if (lane == 0) {
+                            if (p.ost_nbuf > 1) bulk_wait_read1();
+                            else bulk_wait_read();
+                        }
                         __syncwarp();
                     }
                     for (int c0 = 0; c0 < N; c0 += 16) {
@@ -941,7 +950,6 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                     }
                                 }
                             };
-                            const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
                             stage_row(wb, f0);
                             stage_row(wb + p.ost_row, f1);
                             if ((m & 1) == 0) {
@@ -982,7 +990,6 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                         fence_async_smem();
                         __syncwarp();
                         if (lane == 0) {
-                            const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
                             const uint32_t eo = p.out_fp8 ? 1u : 2u, epb = p.pool_fp8 ? 1u : 2u;
                             const int X = x0 + 32 * q;
                             for (uint32_t sb = 0; sb * p.orow_b < (uint32_t)N * eo; ++sb) {
@@ -995,6 +1002,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                                              y >> 1, n);
                             bulk_commit();
                         }
+                        ++oc;
                     }
                 }
             } else {
@@ -1017,9 +1025,13 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     }
                     const size_t pix = ((size_t)n * p.H + y) * p.W + x;
                     float h[4] = {0.f, 0.f, 0.f, 0.f};
-                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp;
-                    if (p.ostage) {  // the staging of the previous row has been read
-                        if (lane == 0) bulk_wait_read();
+                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp +
+                                        (uint32_t)(oc % p.ost_nbuf) * p.ost_unit;
+                    if (p.ostage) {  // the store that last used this staging buffer has read it
+                        if (lane == 0) {
+                            if (p.ost_nbuf > 1) bulk_wait_read1();
+                            else bulk_wait_read();
+                        }
                         __syncwarp();
                     }
                     for (int c0 = 0; c0 < N; c0 += 32) {
@@ -1108,6 +1120,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                             }
                             bulk_commit();
                         }
+                        ++oc;
                     }
                 }
             }
@@ -1173,7 +1186,7 @@ bool encode(CUtensorMap* m, int rank, const void* ptr, const cuuint64_t* dims, c
 
 int g_num_sms = 0;
 int* g_err = nullptr;
-int g_host_err = 0;  // a tensor map could not be encoded: the launch was skipped
+int g_host_err = 0;  // host-side failure of a launch: 4 tensor map, 8 no FP8 configuration, 9 launch refused
 
 }  // namespace
 
@@ -1506,6 +1519,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     const uint8_t* wh = static_cast<const uint8_t*>(whp);
     HParams p;
     std::memset(&p, 0, sizeof(p));
+    p.ost_nbuf = 1;
     const int N = L.cout, c0 = tc_c0(L);
     if (!L.cin1) P = 0;
     else if ((P != 1 && P != 2 && P != 4) || !halo_parity_ok(L, P)) return false;
@@ -1585,9 +1599,11 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     if (O) {
         if (head_out) return false;
         const uint32_t eo = ty.out8 ? 1u : 2u, epb = ty.pool8 ? 1u : 2u;
-        p.ost_warp = halo_ostage_warp(N, pool_out != nullptr, eo, epb);
-        if (!p.ost_warp) return false;
+        p.ost_unit = halo_ostage_warp(N, pool_out != nullptr, eo, epb);
+        if (!p.ost_unit) return false;
         p.ostage = 1;
+        p.ost_nbuf = O >= 2 ? 2 : 1;
+        p.ost_warp = p.ost_nbuf * p.ost_unit;
         p.ost_row = align_up(32u * N * eo, 1024);
         p.ost_pool = (pool_out ? 2u : 1u) * p.ost_row;
         p.orow_b = std::min<uint32_t>((uint32_t)N * eo, 128u);
@@ -1624,6 +1640,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
     }
+    if (stg_total + 2 * p.stage_bytes > 220u * 1024u) return false;  // staging + two pipeline stages must fit
     p.stages = std::min<int>(8, (int)((220u * 1024u - stg_total) / p.stage_bytes));
     (void)halo_stage_bytes;
     if (p.stages < 2) return false;
@@ -1661,6 +1678,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
         kern<<<grid, kHaloThreads, smem, st>>>(p);
+        if (cudaGetLastError() != cudaSuccess) g_host_err = 9;  // a launch that did not start: reported, never silent
     };
     auto pick = [&](auto par) {
         constexpr int PP = decltype(par)::value;
@@ -1724,13 +1742,16 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             halo_default(L, R, P, CK);
             if (ty.in8) CK = std::max(32, CK);
             // untuned: TMA-store epilogue where it fits next to two pipeline stages
-            static const bool no_tma_store = [] {
+            // LNR_CONV_TMA_STORE=0: direct stores; =1: one staging buffer per warp
+            static const int tma_store = [] {
                 const char* e = getenv("LNR_CONV_TMA_STORE");
-                return e && !strcmp(e, "0");
+                return e ? atoi(e) : 2;
             }();
-            if (!no_tma_store &&
-                tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, 1, st, ty))
-                return;
+            if (tma_store > 0)
+                for (int nbuf = std::min(tma_store, 2); nbuf >= 1; --nbuf)
+                    if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, nbuf,
+                                     st, ty))
+                        return;
         }
         if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, cfg.O, st, ty))
             return;
@@ -1779,10 +1800,11 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 const bool fp8 = prec == LNR_FP8;
                 const uint32_t eo = fp8 && !L.out_bf16 ? 1u : 2u, ep = fp8 && !L.pool_bf16 ? 1u : 2u;
                 const uint32_t wst = L.head ? 0u : halo_ostage_warp(N, L.pool, eo, ep);
-                if (wst && sb * 2 + kEpiWarps * wst <= 220u * 1024u) {
-                    c.O = 1;
-                    out.push_back(c);
-                }
+                for (int nbuf = 1; nbuf <= 2; ++nbuf)
+                    if (wst && sb * 2 + kEpiWarps * nbuf * wst <= 220u * 1024u) {
+                        c.O = nbuf;
+                        out.push_back(c);
+                    }
             }
         }
     return out;
