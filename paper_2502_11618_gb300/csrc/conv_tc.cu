@@ -38,12 +38,14 @@ namespace lnr {
 namespace {
 
 constexpr int kThreads = 192;
-// halo kernel: producer warp, kMmaWarps MMA-issuing warps, kEpiWarps epilogue warps.  One thread
+// halo kernel: producer warp, kMmaWarps MMA-issuing warps, EPI (4 or 8) epilogue warps.  One thread
 // issues about one tcgen05.mma per ~120 cycles whatever N is, so small-N convolutions need
 // several issuing threads; each owns disjoint accumulators.
 constexpr int kMmaWarps = 4;
-constexpr int kEpiWarps = 8;  // two per TMEM lane quarter: one warp per scheduler cannot hide the epilogue's latency
-constexpr int kHaloThreads = 32 * (1 + kMmaWarps + kEpiWarps);
+// Epilogue warps, chosen per layer: 4 (one per TMEM lane quarter; 288 threads allow about
+// 160 registers per thread) or 8 (two per quarter, 416 threads, 128 registers: more latency
+// hiding for stores and the fused head's dot products).
+__host__ __device__ constexpr int halo_threads(int epi) { return 32 * (1 + kMmaWarps + epi); }
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
 
@@ -713,15 +715,16 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
 // conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
 // class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
-template <int R, int PAR, bool IN8>
-__global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_constant__ HParams p) {
+template <int R, int PAR, bool IN8, int EPI>
+__global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid_constant__ HParams p) {
+    constexpr int kHaloThreads = halo_threads(EPI);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* const gbase = smem_raw + (base - raw);
     const int S = p.stages;
     const uint32_t stg = base + S * p.stage_bytes;  // epilogue staging (TMA stores), 1024-aligned
-    const uint32_t bars = stg + (p.ostage ? kEpiWarps * p.ost_warp : 0u);
+    const uint32_t bars = stg + (p.ostage ? EPI * p.ost_warp : 0u);
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (S + s); };
     auto tfull = [&](int b) { return bars + 8u * (2 * S + b); };
@@ -742,7 +745,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull(b), p.nmma);
-            mbar_init(tempty(b), kEpiWarps);
+            mbar_init(tempty(b), EPI);
         }
         mbar_init(drain, p.nmma);
         *flag = 0;
@@ -868,7 +871,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
         const int m = 32 * q + lane;
-        const int eh = (warp - kMmaWarps - 1) >> 2;  // which of the two warps of this lane quarter
+        constexpr int NE = EPI / 4;                   // warps per TMEM lane quarter
+        const int eh = (warp - kMmaWarps - 1) >> 2;  // which of them this warp is
         const bool leader = threadIdx.x == 32 * (kMmaWarps + 1);
         const int Wh = p.W >> 1, Hh = p.H >> 1;
         const bool pool = p.pool_out != nullptr;
@@ -896,7 +900,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
         for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tcount) {
             const int b = tcount & 1;
             if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
-            named_sync(1, 32 * kEpiWarps);
+            named_sync(1, 32 * EPI);
             if (*flag) break;
             tc_fence_after();
             int n, x0, y0, px, py;
@@ -904,9 +908,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
             constexpr int NCE = PAR == 0 ? 1 : PAR;
             const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NCE * R * N);
             if (pool) {
-                // rows in pairs (pairs alternate between the quarter's two warps): both rows
+                // rows in pairs (pairs alternate between the quarter's warps): both rows
                 // stored, their 2x2 maximum pooled with the lane holding the next column
-                for (int r = 2 * eh; r < R; r += 4) {
+                for (int r = 2 * eh; r < R; r += 2 * NE) {
                     const int x = x0 + m, y = y0 + r;
                     const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
                     const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp +
@@ -1006,7 +1010,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1) k_conv_halo(const __grid_cons
                     }
                 }
             } else {
-                for (int a = eh; a < NCE * R; a += 2) {
+                for (int a = eh; a < NCE * R; a += NE) {
                     int x, y;
                     bool v;
                     if (PAR) {
@@ -1511,7 +1515,7 @@ struct HaloTypes {
 
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
-                  int P, int ckmax, int O, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
+                  int P, int ckmax, int O, int E, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
     const int esize = ty.in8 ? 1 : 2;
     if (ty.in8 && ckmax < 32) return false;
     const void* whp = ty.in8 ? L.wh8[ckmax == 32 ? 0 : ckmax == 64 ? 1 : 2] : L.wh[ck_index(ckmax)];
@@ -1594,6 +1598,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.ntiles = B * p.tiles_y * p.tiles_x;
     }
     p.stage_bytes = stage;
+    const int epi = E == 4 ? 4 : 8;  // epilogue warps
     // epilogue stores through staging + TMA (no fused head: its outputs are per-pixel floats)
     uint32_t stg_total = 0;
     if (O) {
@@ -1610,7 +1615,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.prow_b = std::min<uint32_t>((uint32_t)N * epb, 128u);
         p.omask = p.orow_b == 128 ? 7u : p.orow_b == 64 ? 3u : 1u;
         p.pmask = p.prow_b == 128 ? 7u : p.prow_b == 64 ? 3u : 1u;
-        stg_total = kEpiWarps * p.ost_warp;
+        stg_total = epi * p.ost_warp;
         cuuint32_t es[5] = {1, 1, 1, 1, 1};
         const CUtensorMapDataType odt = ty.out8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         const cuuint64_t ro = (cuuint64_t)N * eo;
@@ -1669,7 +1674,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16 +
                         4 * (size_t)(2 * N + (head_out ? 4 * (N + 1) : 0));
     const int grid = std::min(p.ntiles, g_num_sms);
-    auto launch = [&](void (*kern)(HParams)) {
+    auto launch = [&](void (*kern)(HParams), int threads) {
         static std::mutex mu;
         static std::set<const void*> done;
         {
@@ -1677,26 +1682,30 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             if (done.insert((const void*)kern).second)
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
-        kern<<<grid, kHaloThreads, smem, st>>>(p);
+        kern<<<grid, threads, smem, st>>>(p);
         if (cudaGetLastError() != cudaSuccess) g_host_err = 9;  // a launch that did not start: reported, never silent
     };
-    auto pick = [&](auto par) {
-        constexpr int PP = decltype(par)::value;
+    auto pick4 = [&](auto par, auto ep) {
+        constexpr int PP = decltype(par)::value, EE = decltype(ep)::value;
         if (ty.in8) {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, true>); break;
-                case 2: launch(k_conv_halo<2, PP, true>); break;
-                case 4: launch(k_conv_halo<4, PP, true>); break;
-                default: launch(k_conv_halo<8, PP, true>); break;
+                case 1: launch(k_conv_halo<1, PP, true, EE>, halo_threads(EE)); break;
+                case 2: launch(k_conv_halo<2, PP, true, EE>, halo_threads(EE)); break;
+                case 4: launch(k_conv_halo<4, PP, true, EE>, halo_threads(EE)); break;
+                default: launch(k_conv_halo<8, PP, true, EE>, halo_threads(EE)); break;
             }
         } else {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, false>); break;
-                case 2: launch(k_conv_halo<2, PP, false>); break;
-                case 4: launch(k_conv_halo<4, PP, false>); break;
-                default: launch(k_conv_halo<8, PP, false>); break;
+                case 1: launch(k_conv_halo<1, PP, false, EE>, halo_threads(EE)); break;
+                case 2: launch(k_conv_halo<2, PP, false, EE>, halo_threads(EE)); break;
+                case 4: launch(k_conv_halo<4, PP, false, EE>, halo_threads(EE)); break;
+                default: launch(k_conv_halo<8, PP, false, EE>, halo_threads(EE)); break;
             }
         }
+    };
+    auto pick = [&](auto par) {
+        if (epi == 8) pick4(par, std::integral_constant<int, 8>{});
+        else pick4(par, std::integral_constant<int, 4>{});
     };
     switch (P) {
         case 0: pick(std::integral_constant<int, 0>{}); break;
@@ -1750,10 +1759,11 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             if (tma_store > 0)
                 for (int nbuf = std::min(tma_store, 2); nbuf >= 1; --nbuf)
                     if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, nbuf,
-                                     st, ty))
+                                     8, st, ty))
                         return;
         }
-        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, cfg.O, st, ty))
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, cfg.O,
+                         cfg.mode == 0 ? 8 : cfg.E, st, ty))
             return;
         if (fp8) {  // no fallback for FP8: record and skip
             g_host_err = 8;
@@ -1790,21 +1800,24 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 last_ck[1] = c1;
                 const uint32_t sb = halo_stage_bytes(L, r, P, ck, esize);
                 if (sb * 2 > 220u * 1024u) continue;
-                TcConfig c;
-                c.mode = 1;
-                c.R = r;
-                c.P = P;
-                c.CK = ck;
-                out.push_back(c);
-                // the same tile with the TMA-store epilogue, where its staging fits
-                const bool fp8 = prec == LNR_FP8;
-                const uint32_t eo = fp8 && !L.out_bf16 ? 1u : 2u, ep = fp8 && !L.pool_bf16 ? 1u : 2u;
-                const uint32_t wst = L.head ? 0u : halo_ostage_warp(N, L.pool, eo, ep);
-                for (int nbuf = 1; nbuf <= 2; ++nbuf)
-                    if (wst && sb * 2 + kEpiWarps * nbuf * wst <= 220u * 1024u) {
-                        c.O = nbuf;
-                        out.push_back(c);
-                    }
+                for (int e : {4, 8}) {
+                    TcConfig c;
+                    c.mode = 1;
+                    c.R = r;
+                    c.P = P;
+                    c.CK = ck;
+                    c.E = e;
+                    out.push_back(c);
+                    // the same tile with the TMA-store epilogue, where its staging fits
+                    const bool fp8 = prec == LNR_FP8;
+                    const uint32_t eo = fp8 && !L.out_bf16 ? 1u : 2u, ep = fp8 && !L.pool_bf16 ? 1u : 2u;
+                    const uint32_t wst = L.head ? 0u : halo_ostage_warp(N, L.pool, eo, ep);
+                    for (int nbuf = 1; nbuf <= 2; ++nbuf)
+                        if (wst && sb * 2 + (uint32_t)e * nbuf * wst <= 220u * 1024u) {
+                            c.O = nbuf;
+                            out.push_back(c);
+                        }
+                }
             }
         }
     return out;

@@ -40,7 +40,8 @@ struct ViewDev {
 struct TcConfig {
     int mode = 0;
     int R = 0, P = 0, CK = 0;
-    int O = 0;  // halo kernel: 1 = epilogue stores through shared-memory staging and TMA
+    int O = 0;  // halo kernel: 1 or 2 = epilogue stores through that many staging buffers and TMA
+    int E = 8;  // halo kernel: epilogue warps (4 or 8)
 };
 
 // One convolution as the GPU runs it.
