@@ -496,8 +496,10 @@ __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
         __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
         pw[j] = *reinterpret_cast<uint32_t*>(&b2);
     }
-    reinterpret_cast<uint4*>(dst)[0] = pk[0];
-    reinterpret_cast<uint4*>(dst)[1] = pk[1];
+    // one 32-byte store (dst is 32-byte aligned: 16 channels at a multiple of 16)
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(pw[0]), "r"(pw[1]), "r"(pw[2]),
+                 "r"(pw[3]), "r"(pw[4]), "r"(pw[5]), "r"(pw[6]), "r"(pw[7])
+                 : "memory");
 }
 
 // 16 channels packed for a 16-byte-chunk store: BF16 (two chunks) or E4M3 of v * inv (one).
@@ -516,6 +518,16 @@ __device__ __forceinline__ uint4 pack_fp8x16(const float* v, float inv) {
     for (int j = 0; j < 8; ++j)
         ph[j] = __nv_cvt_float2_to_fp8x2(make_float2(v[2 * j] * inv, v[2 * j + 1] * inv), __NV_SATFINITE, __NV_E4M3);
     return pk;
+}
+
+// Packed FP32 pair (lo, hi) and its fused multiply-add d = a * b + c, lane by lane (IEEE fma).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
 // Epilogue staging for TMA stores: 16 bytes at byte `off` of a 1024-aligned staging box
@@ -1069,29 +1081,21 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                                 }
                             }
                         } else if (p.head_out) {
+                            // 1x1 head: 4 outputs (zero weights past head_o), channel pairs
+                            // accumulated with packed FP32x2 fused multiply-adds
 #pragma unroll
-                            for (int o = 0; o < 4; ++o) {  // 4 independent chains (zero weights past head_o)
+                            for (int o = 0; o < 4; ++o) {
                                 const float4* w4 = reinterpret_cast<const float4*>(shw + o * N + c0);
-                                float sacc = 0.f;
+                                uint64_t acc = 0;  // (0.f, 0.f)
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) {
+                                for (int j = 0; j < 8; ++j) {
+                                    if (j >= 4 && !two) break;
                                     const float4 wv = w4[j];
-                                    sacc = fmaf(wv.x, f0[4 * j], sacc);
-                                    sacc = fmaf(wv.y, f0[4 * j + 1], sacc);
-                                    sacc = fmaf(wv.z, f0[4 * j + 2], sacc);
-                                    sacc = fmaf(wv.w, f0[4 * j + 3], sacc);
+                                    const float* f = j < 4 ? f0 + 4 * j : f1 + 4 * (j - 4);
+                                    acc = fma2(pack2(wv.x, wv.y), pack2(f[0], f[1]), acc);
+                                    acc = fma2(pack2(wv.z, wv.w), pack2(f[2], f[3]), acc);
                                 }
-                                if (two) {
-#pragma unroll
-                                    for (int j = 0; j < 4; ++j) {
-                                        const float4 wv = w4[4 + j];
-                                        sacc = fmaf(wv.x, f1[4 * j], sacc);
-                                        sacc = fmaf(wv.y, f1[4 * j + 1], sacc);
-                                        sacc = fmaf(wv.z, f1[4 * j + 2], sacc);
-                                        sacc = fmaf(wv.w, f1[4 * j + 3], sacc);
-                                    }
-                                }
-                                h[o] += sacc;
+                                h[o] += __uint_as_float((uint32_t)acc) + __uint_as_float((uint32_t)(acc >> 32));
                             }
                         } else if (v) {
                             if (p.out_fp8) {
@@ -1107,7 +1111,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
 #pragma unroll
                         for (int o = 0; o < 4; ++o) {
                             if (o >= p.head_o) break;
-                            p.head_out[pix * p.head_o + o] = 1.0f / (1.0f + expf(-(h[o] + shw[4 * N + o])));
+                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + shw[4 * N + o])));
                         }
                     }
                     if (p.ostage) {  // the row leaves by TMA (clipped at the image edges)
