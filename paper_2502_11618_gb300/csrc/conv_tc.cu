@@ -488,6 +488,13 @@ __device__ __forceinline__ void st_fp8x16(uint8_t* dst, const float* v, float in
     *reinterpret_cast<uint4*>(dst) = pk;
 }
 
+// 32 bytes to a 32-byte-aligned global address in one store.
+__device__ __forceinline__ void st_32b(void* dst, uint4 a, uint4 b) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
     uint4 pk[2];
     uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
@@ -1099,8 +1106,11 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                             }
                         } else if (v) {
                             if (p.out_fp8) {
-                                st_fp8x16(static_cast<uint8_t*>(p.out) + pix * N + c0, f0, p.inv_out);
-                                if (two) st_fp8x16(static_cast<uint8_t*>(p.out) + pix * N + c0 + 16, f1, p.inv_out);
+                                uint8_t* d8 = static_cast<uint8_t*>(p.out) + pix * N + c0;
+                                if (two)  // 32 E4M3 channels in one 32-byte store (N is a multiple of 32)
+                                    st_32b(d8, pack_fp8x16(f0, p.inv_out), pack_fp8x16(f1, p.inv_out));
+                                else
+                                    st_fp8x16(d8, f0, p.inv_out);
                             } else {
                                 st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0, f0);
                                 if (two) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0 + 16, f1);
