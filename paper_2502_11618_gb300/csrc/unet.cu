@@ -396,8 +396,8 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
         (p == LNR_FP8 ? L.tuned8 : L.tuned)[{k.W, k.H}] = best_cfg;
         static const bool log = getenv("LNR_TUNE_LOG") != nullptr;
         if (log)
-            fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d  %.1f us\n", k.layer, k.W, k.H,
-                    best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, 1e3 * best / reps);
+            fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d C %d  %.1f us\n", k.layer, k.W, k.H,
+                    best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, best_cfg.C, 1e3 * best / reps);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

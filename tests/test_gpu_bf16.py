@@ -117,14 +117,25 @@ assert worst <= 2e-2
 """
 
 
-@pytest.mark.parametrize("kernel", ["generic", "halo"])
+_VARIANTS = {
+    "generic": dict(LNR_CONV_KERNEL="generic"),
+    "halo": dict(LNR_CONV_KERNEL="halo"),
+    "halo_direct_stores": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMA_STORE="0"),
+    "halo_one_staging_buffer": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMA_STORE="1"),
+    "halo_cta_pairs": dict(LNR_CONV_KERNEL="halo", LNR_CONV_CLUSTER="1"),
+}
+
+
+@pytest.mark.parametrize("kernel", list(_VARIANTS))
 def test_bf16_each_conv_kernel(lnr, kernel):
-    """Both tensor-core conv kernels (forced for every layer) meet the BF16 bars."""
+    """Every tensor-core conv variant (forced for every layer it applies to) meets the BF16
+    bars: the generic kernel; the halo kernel with staged TMA stores (two or one buffers),
+    with direct stores, and with CTA pairs sharing weight stages."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, LNR_CONV_KERNEL=kernel)
+    env = dict(os.environ, **_VARIANTS[kernel])
     r = subprocess.run([sys.executable, "-c", _KERNEL_SCRIPT.format(root=root)], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
