@@ -478,6 +478,8 @@ struct HParams {
     int head_o;
     int* err;
     int cluster;  // 1: CTA pairs (clusters of 2) stage every chunk's weights once for both (TMA multicast)
+    int vtiles;   // tiles the CTAs step through: ntiles, or (pairs) padded so that both CTAs of a
+                  // pair run the same count and, for 2 parity classes, share the tile's y class
     // TMA-store epilogue (ostage = 1): per epilogue warp a staging area of ost_warp bytes at
     // ost_off from the 1024-aligned base: (pool ? 2 : 1) rows of 32 pixels x N channels,
     // then (pool) 16 pooled pixels, every part 1024-aligned; rows split into boxes of
@@ -741,8 +743,7 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
                         const int r = u / NY, cy = PAR == 4 ? u - r * NY : q.py;
                         const uint32_t du = d0 + (uint32_t)(u * NX) * N;
                         const uint32_t ar = a0 + (uint32_t)(r + cy + j) * row16 + 2 * k;
-                        // staged coarse blocks: all 16 (PAR 4, CTA pairs) or the tile's y class's 8
-                        const uint32_t bj = b0 + (uint32_t)((PAR == 4 || !s.bsel ? 8 * cy : 0) + 4 * j) * btap + 2 * k;
+                        const uint32_t bj = b0 + (uint32_t)((PAR == 4 ? 8 * cy : 0) + 4 * j) * btap + 2 * k;
                         if (NX == 2) {
                             mma_op<IN8>(du, hi | (uint64_t)(ar + 2 * pitch16), hi | (uint64_t)bj, q.idesc, 1u);
                             mma_op<IN8>(du, hi | (uint64_t)(ar + pitch16), hi | (uint64_t)(bj + btap), id2, 1u);
@@ -818,22 +819,33 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
     // (their weight stages are shared): the pair continues while its even tile exists, and
     // a CTA whose tile is past the end runs it on zero-filled input without storing it.
     const int rank = p.cluster ? (int)cluster_rank() : 0;
-    auto tile_live = [&](int t) { return t - rank < p.ntiles; };
+    (void)rank;
+    auto tile_live = [&](int t) { return t < p.vtiles; };
 
     // tile t -> image n, first column x0 and first row y0 (coarse for parity tiles) and the
     // parity class (px, py); parity is the fastest index so that the four classes of a
     // region run back to back and share its halo in L2
     // (for PAR 1 and 2, px / py are the tile's class; PAR 4 covers every class)
-    auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
+    // A tile past the real ones (CTA pairs' padding) reports valid = false; its loads start
+    // past the last image and read zeros.
+    auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py, bool& valid) {
         px = py = 0;
+        valid = t < p.ntiles;
         if (PAR == 1) {
             px = t & 1;
             py = (t >> 1) & 1;
             t >>= 2;
         } else if (PAR == 2) {
-            py = t & 1;
-            t >>= 1;
+            if (p.cluster) {  // the two tiles of a pair (t, t + 1) share the y class
+                py = (t >> 1) & 1;
+                t = ((t >> 2) << 1) | (t & 1);
+                valid = t < (p.ntiles >> 1);
+            } else {
+                py = t & 1;
+                t >>= 1;
+            }
         }
+        if (!valid) t = p.tiles_x * p.tiles_y * p.B;  // image index B: every load reads zeros
         const int tx = t % p.tiles_x;
         t /= p.tiles_x;
         const int ty = t % p.tiles_y;
@@ -848,7 +860,8 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         bool ok = true;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x) {
             int n, x0, y0, px, py;
-            tile_of(t, n, x0, y0, px, py);  // past the end: n >= B, zero-filled
+            bool valid;
+            tile_of(t, n, x0, y0, px, py, valid);  // padding tile: n = B, zero-filled
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
                 for (int cc = 0; cc < s.nchunk; ++cc) {
@@ -864,13 +877,14 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                     } else {
                         tma_4d(a_dst, &s.a, full(st), c, x0 - 1, y0 - 1, n);
                     }
+                    const int wb0 = cc * s.wblk + (s.bsel ? 8 * py : 0);  // first weight block of the stage
                     if (!p.cluster) {
-                        tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, cc * s.wblk + (s.bsel ? 8 * py : 0));
+                        tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, wb0);
                     } else if (rank == 0) {  // each CTA of the pair stages part of the blocks for both
-                        tma_3d_mc(a_dst + s.b_off, &s.b, full(st), 0, 0, cc * s.wblk, (uint16_t)3);
+                        tma_3d_mc(a_dst + s.b_off, &s.b, full(st), 0, 0, wb0, (uint16_t)3);
                     } else {
-                        tma_3d_mc(a_dst + s.b_off + (uint32_t)s.bsplit * N * s.pitch, &s.b2, full(st), 0, 0,
-                                  cc * s.wblk + s.bsplit, (uint16_t)3);
+                        tma_3d_mc(a_dst + s.b_off + (uint32_t)s.bsplit * N * s.pitch, &s.b2, full(st), 0, 0, wb0 + s.bsplit,
+                                  (uint16_t)3);
                     }
                     ++use;
                 }
@@ -893,7 +907,8 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         bool ok = true, issued = false;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
-            tile_of(t, n, x0, y0, px, py);
+            bool valid;
+            tile_of(t, n, x0, y0, px, py, valid);
             q.px = px;
             q.py = py;
             const int b = tcount & 1;
@@ -966,8 +981,9 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
             if (*flag) break;
             tc_fence_after();
             int n, x0, y0, px, py;
-            tile_of(t, n, x0, y0, px, py);
-            if (t >= p.ntiles) {  // the pair's filler tile: nothing to store
+            bool valid;
+            tile_of(t, n, x0, y0, px, py, valid);
+            if (!valid) {  // a CTA pair's padding tile: nothing to store
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty(b));
@@ -1524,7 +1540,8 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
-        const int bl = pairs ? (kind == 2 ? 16 : 9) : halo_bload(kind, P);
+        const int bl = halo_bload(kind, P);
+        (void)pairs;  // CTA pairs stage the same blocks (tiles of a pair share the y class)
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)bl * L.cout * pitch, 1024));
     }
     return st;
@@ -1617,11 +1634,9 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.a_bytes = planes * (uint32_t)s.rows * kHaloW * s.pitch;
         s.b_off = planes * s.plane;
         s.wblk = kind == 2 ? 16 : 9;
-        // CTA pairs share one weight stage: their tiles may differ in y class, so the coarse
-        // operand stages all 16 blocks
-        s.bload = pairs ? (kind == 2 ? 16 : 9) : halo_bload(kind, P);
-        s.bsel = !pairs && kind == 2 && P != 4;
-        s.bsplit = s.bload / 2;
+        s.bload = halo_bload(kind, P);
+        s.bsel = kind == 2 && P != 4;
+        s.bsplit = s.bload / 2;  // CTA pairs: the rank-0 CTA stages the first bsplit blocks for both
         const uint32_t b_bytes = (uint32_t)s.bload * N * s.pitch;
         s.bytes = s.a_bytes + b_bytes;
         stage = std::max(stage, align_up(s.b_off + b_bytes, 1024));
@@ -1748,7 +1763,11 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.err = g_err;
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16 +
                         4 * (size_t)(2 * N + (head_out ? 4 * (N + 1) : 0));
-    const int grid = pairs ? std::min((p.ntiles + 1) & ~1, g_num_sms & ~1) : std::min(p.ntiles, g_num_sms);
+    // CTA pairs step through padded tile counts: with 2 parity classes the (position, class)
+    // tiles pair two positions of one class, 4 * ceil(positions / 2) in all; otherwise the
+    // count rounded up to even
+    p.vtiles = !pairs ? p.ntiles : P == 2 ? 4 * ((p.ntiles / 2 + 1) / 2) : (p.ntiles + 1) & ~1;
+    const int grid = pairs ? std::min(p.vtiles, g_num_sms & ~1) : std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams), int threads) {
         static std::mutex mu;
         static std::set<const void*> done;
