@@ -130,6 +130,28 @@ def peaks():
         return {}
 
 
+# DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
+# (8 x 1080p views, BF16), from one ncu capture (profiles/traffic_multiroom20M_1080p_b8.md).
+# It describes the conv kernels as captured: reported only while their sources are unchanged.
+CONV_TRAFFIC = {"bytes_per_step": 14278.0e6,
+                "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
+                           "de42a98e404aa7746cc2e23691dbffd9388de75cd81b1178a50bed83c81a4959",
+                           "paper_2502_11618_gb300/csrc/unet.cu":
+                           "13b937af77c5fc6470bc1d39ff3927d6aec657cd515c46df58d18f73c86ae004"}}
+
+
+def conv_traffic():
+    import hashlib
+    for rel, digest in CONV_TRAFFIC["sha256"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return CONV_TRAFFIC["bytes_per_step"]
+
+
 def make_workload(device):
     import synth
     from synth.workloads import MULTIROOM_20M, make_scene
@@ -404,7 +426,8 @@ def main():
                 "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = conv_traffic() if have_tc else None
+    roof["traffic_scope"] = "DRAM bytes read + written by all U-Net conv launches of one step (ncu)"
 
     # ---- plain per-frame FP32 path (device-timed) ----------------------------------
     r.set_precision("fp32")
