@@ -127,6 +127,42 @@ lnr_status lnr_training_input(lnr_ctx* ctx, const lnr_view* view, const lnr_intr
                               int W, int H, int n_levels, float fs, const float* gt_rgb,
                               int unfiltered, float* out);
 
+/* ---- cloud shards: one cloud split over several contexts (GPUs) ----
+ * A cloud too large for one GPU is split by cells: every shard holds the points of a range
+ * of cells of one common grid frame.  Each shard splats its points into z-buffer keys
+ * (lnr_render_stage, LNR_STAGE_KEYS) whose position field is the point's position in the
+ * whole cloud's sorted order (lnr_set_shard).  The element-wise minimum of the shards' keys
+ * is the whole cloud's z-buffer, bit for bit.  Each shard resolves the colours of its own
+ * front points (lnr_shard_resolve); the element-wise sum (or maximum) of the shards'
+ * colours is the whole cloud's.  Any one context then finishes the frame
+ * (lnr_shard_finish).  The two exchanges (a u64 min and a u32 sum over the shards) belong
+ * to the caller, e.g. NCCL all-reduces.  Not with the soft z-buffer. */
+
+/* Build the grid in a given frame (cell size, origin g0[3] FP64, dims[3] cells), as
+ * lnr_build_grid would for the whole cloud (lnr_grid_info of a context holding it, or the
+ * same formulas): points are sorted by cell as usual, points outside the frame go to its
+ * border cells.  Errors: LNR_E_STATE before load_cloud; LNR_E_ARG for a bad frame. */
+lnr_status lnr_build_grid_frame(lnr_ctx* ctx, double cell_size, const double* g0, const int32_t* dims);
+
+/* Make this context a cloud shard: key positions are its sorted positions + pos_base (the
+ * number of the whole cloud's points in the cells before this shard's), and the resolve
+ * colours only keys inside [pos_base, pos_base + n).  0 (the default) for a whole cloud.
+ * Errors: LNR_E_ARG when positions would exceed 32 bits; LNR_E_STATE while serving. */
+lnr_status lnr_set_shard(lnr_ctx* ctx, uint32_t pos_base);
+
+/* A shard's colours for the whole cloud's keys.  keys: device, H*W uint64 (the shards'
+ * minimum); rgba: device, H*W uint32 written: r | g << 8 | b << 16 | 1 << 24 where the
+ * front point is this shard's, 0 elsewhere.  view / intr / W / H as lnr_render. */
+lnr_status lnr_shard_resolve(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                             int H, const uint64_t* keys, uint32_t* rgba);
+
+/* The frame from the whole cloud's keys and colours (device buffers as above): depth
+ * filter (Fig. 2) with n_levels / fs, U-Net, out_rgb as lnr_render (host, or device when
+ * out_on_device).  Equals lnr_render of a context holding the whole cloud, bit for bit. */
+lnr_status lnr_shard_finish(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                            int H, int n_levels, float fs, const uint64_t* keys, const uint32_t* rgba,
+                            float* out_rgb, int out_on_device);
+
 /* Collision rule of the splat (Sec. 3, "Point Cloud Projection").  rel = 0 (the default):
  * hard z-buffer, each pixel keeps its nearest point (depth ties: lower sorted position).
  * rel > 0: soft z-buffer, the pixel's colour is the per-channel integer mean, rounded half

@@ -90,16 +90,22 @@ class Grid:
         return int(np.prod(self.dims.astype(np.int64)))
 
 
-def build_grid(xyz, rgb, scan_id, cell) -> Grid:
+def build_grid(xyz, rgb, scan_id, cell, frame=None) -> Grid:
+    """Grid of the cloud; frame = (g0, dims) builds it in a given frame (another cloud's,
+    e.g. the whole cloud's for a shard of it) instead of the cloud's own bounds."""
     L = lib()
     xyz = _c(xyz, np.float64)
     rgb = _c(rgb, np.uint8)
     scan = None if scan_id is None else _c(scan_id, np.uint8)
     n = xyz.shape[0]
-    g0 = np.zeros(3, np.float64)
-    dims = np.zeros(3, np.int32)
-    if L.orc_grid_dims(_ptr(xyz), n, float(cell), _ptr(g0), _ptr(dims)) != 0:
-        raise ValueError("bad cloud or cell size")
+    if frame is not None:
+        g0 = _c(frame[0], np.float64).copy()
+        dims = _c(frame[1], np.int32).copy()
+    else:
+        g0 = np.zeros(3, np.float64)
+        dims = np.zeros(3, np.int32)
+        if L.orc_grid_dims(_ptr(xyz), n, float(cell), _ptr(g0), _ptr(dims)) != 0:
+            raise ValueError("bad cloud or cell size")
     nc = int(np.prod(dims.astype(np.int64)))
     cs = np.zeros(nc + 1, np.uint32)
     order = np.zeros(n, np.uint32)

@@ -26,7 +26,8 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
            "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer",
-           "lnr_training_input"]
+           "lnr_training_input", "lnr_build_grid_frame", "lnr_set_shard", "lnr_shard_resolve",
+           "lnr_shard_finish"]
 
 
 class LnrError(RuntimeError):
@@ -72,6 +73,10 @@ def lib():
             "lnr_set_unet": ([p, C.POINTER(UnetDesc), p, sz, i], st),
             "lnr_set_precision": ([p, i], st),
             "lnr_set_soft_zbuffer": ([p, f], st),
+            "lnr_build_grid_frame": ([p, d, p, p], st),
+            "lnr_set_shard": ([p, C.c_uint32], st),
+            "lnr_shard_resolve": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, p, p], st),
+            "lnr_shard_finish": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, p, p, i], st),
             "lnr_training_input": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, i, p], st),
             "lnr_render": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, i], st),
             "lnr_render_stage": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, i, p, i], st),
@@ -158,6 +163,33 @@ class Renderer:
 
     def build_grid(self, cell_size: float):
         self._check(self._L.lnr_build_grid(self._c, float(cell_size)))
+
+    def build_grid_frame(self, cell_size, g0, dims):
+        """Grid in a given frame (another context's grid_info): cloud shards share one."""
+        g = np.ascontiguousarray(g0, dtype=np.float64)
+        dm = np.ascontiguousarray(dims, dtype=np.int32)
+        self._check(self._L.lnr_build_grid_frame(self._c, float(cell_size), _ptr(g), _ptr(dm)))
+
+    def set_shard(self, pos_base):
+        """Key positions offset by pos_base: this context holds a shard of a larger cloud."""
+        self._check(self._L.lnr_set_shard(self._c, C.c_uint32(int(pos_base))))
+
+    def shard_resolve(self, view, intr, W, H, keys_dev, rgba_dev):
+        """Colours of this shard's front points for the whole cloud's keys (device tensors:
+        keys uint64/int64 [H*W], rgba int32/uint32 [H*W], written)."""
+        self._check(self._L.lnr_shard_resolve(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)), W, H,
+                                               C.c_void_p(keys_dev.data_ptr()), C.c_void_p(rgba_dev.data_ptr())))
+
+    def shard_finish(self, view, intr, W, H, n_levels, fs, keys_dev, rgba_dev, out=None):
+        """The frame from the whole cloud's keys and colours (device tensors); (H, W, 3)."""
+        host = out is None
+        if host:
+            out = np.empty((H, W, 3), np.float32)
+        ptr = _ptr(out) if host else C.c_void_p(out.data_ptr())
+        self._check(self._L.lnr_shard_finish(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)), W, H,
+                                              n_levels, float(fs), C.c_void_p(keys_dev.data_ptr()),
+                                              C.c_void_p(rgba_dev.data_ptr()), ptr, 0 if host else 1))
+        return out
 
     def grid_info(self):
         g0 = np.zeros(3, np.float64)

@@ -177,6 +177,22 @@ void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_pr
     mark(5);
 }
 
+void enqueue_from_keys(lnr_ctx* c, Workspace& ws, cudaStream_t st, const uint64_t* keys, const uint32_t* rgba,
+                       int stage, lnr_precision prec) {
+    const size_t P = (size_t)ws.W * ws.H;
+    cudaMemcpyAsync(ws.view.p, ws.pinned_view.p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws.keys.p, keys, 8 * P, cudaMemcpyDeviceToDevice, st);
+    launch_resolve_pyramid(c, ws, st);  // depth, pyramid, this context's colours; clears the keys
+    if (rgba) cudaMemcpyAsync(ws.rgba.p, rgba, 4 * P, cudaMemcpyDeviceToDevice, st);
+    if (stage == LNR_STAGE_RGBDA_RAW) return;
+    const int kind = (stage >= 0) ? 0 : unet_in_kind(prec);
+    void* unet_in = ws.act[4 * kMaxUnetLevels].p;
+    for (int l = ws.nlev - 1; l >= 1; --l) launch_upsample(c, ws, l, nullptr, 2, false, st);
+    launch_upsample(c, ws, 0, unet_in, kind, stage == LNR_STAGE_FILTERED, st);
+    if (stage >= 0) return;
+    unet_forward(c, ws, prec, unet_in, ws.out.as<float>(), st, nullptr);
+}
+
 lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in,
                                 int W, int H, int nlev, const float* fs) {
     cudaError_t e = ensure_ws(c, ws, B, W, H, nlev);
@@ -355,6 +371,35 @@ lnr_status lnr_load_cloud(lnr_ctx* c, const double* xyz, const uint8_t* rgb, con
     return LNR_OK;
 }
 
+// Grid build in a given frame (origin g0, dims cells of size cell): points outside it are
+// clamped into its border cells.
+static lnr_status build_grid_in(lnr_ctx* c, double cell, const double g0[3], const int32_t dims[3]) {
+    double total = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || !std::isfinite(g0[a])) return fail(c, LNR_E_ARG, "bad grid frame");
+        total *= (double)dims[a];
+    }
+    if (total > 2147483647.0) return fail(c, LNR_E_ARG, "too many cells (> 2^31)");
+    std::memcpy(c->g0, g0, sizeof(c->g0));
+    std::memcpy(c->dims, dims, sizeof(c->dims));
+    c->cell = cell;
+    c->ncells = (int64_t)total;
+    cudaError_t e = grid_build(c, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "grid build");
+    c->grid_ok = true;
+    c->cloud_gen++;
+    c->ws.keys_dirty = true;
+    return LNR_OK;
+}
+
+lnr_status lnr_build_grid_frame(lnr_ctx* c, double cell, const double* g0, const int32_t* dims) {
+    if (!c || !g0 || !dims) return LNR_E_ARG;
+    if (!c->n) return fail(c, LNR_E_STATE, "build_grid before load_cloud");
+    if (!(cell > 0.0) || !std::isfinite(cell)) return fail(c, LNR_E_ARG, "cell size must be > 0");
+    cudaSetDevice(c->device);
+    return build_grid_in(c, cell, g0, dims);
+}
+
 lnr_status lnr_build_grid(lnr_ctx* c, double cell) {
     if (!c) return LNR_E_ARG;
     if (!c->n) return fail(c, LNR_E_STATE, "build_grid before load_cloud");
@@ -367,22 +412,75 @@ lnr_status lnr_build_grid(lnr_ctx* c, double cell) {
     e = grid_bbox(c->xyz.as<double>(), c->n, tmp.as<double>(), lohi, c->stream);
     tmp.release();
     if (e != cudaSuccess) return cuda_fail(c, e, "grid bounds");
-    double total = 1.0;
+    double g0[3];
+    int32_t dims[3];
     for (int a = 0; a < 3; ++a) {
-        c->g0[a] = std::floor(lohi[a] / cell) * cell;
-        double d = std::floor((lohi[3 + a] - c->g0[a]) / cell) + 1.0;
+        g0[a] = std::floor(lohi[a] / cell) * cell;
+        const double d = std::floor((lohi[3 + a] - g0[a]) / cell) + 1.0;
         if (d > 2147483647.0) return fail(c, LNR_E_ARG, "too many cells");
-        c->dims[a] = (int32_t)d;
-        total *= d;
+        dims[a] = (int32_t)d;
     }
-    if (total > 2147483647.0) return fail(c, LNR_E_ARG, "too many cells (> 2^31)");
-    c->cell = cell;
-    c->ncells = (int64_t)total;
-    e = grid_build(c, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "grid build");
-    c->grid_ok = true;
-    c->cloud_gen++;
-    c->ws.keys_dirty = true;
+    return build_grid_in(c, cell, g0, dims);
+}
+
+lnr_status lnr_set_shard(lnr_ctx* c, uint32_t pos_base) {
+    if (!c) return LNR_E_ARG;
+    if (c->server) return fail(c, LNR_E_STATE, "cannot change the shard while serving");
+    if ((uint64_t)pos_base + c->n > 0xffffffffull) return fail(c, LNR_E_ARG, "shard positions exceed 32 bits");
+    if (pos_base != c->shard_base) {
+        c->shard_base = pos_base;
+        c->cloud_gen++;  // captured frame graphs hold the old base
+    }
+    return LNR_OK;
+}
+
+// One cloud shard's resolve against the whole cloud's z-buffer keys (device, H*W): the
+// colours (r | g << 8 | b << 16 | 1 << 24) of the pixels whose front point is this shard's,
+// zero elsewhere, into rgba (device, H*W).
+lnr_status lnr_shard_resolve(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H,
+                             const uint64_t* keys, uint32_t* rgba) {
+    if (!c) return LNR_E_ARG;
+    const float fs = 0.0f;
+    lnr_status s = check_frame_args(c, 1, view, in, W, H, 0, &fs, false);
+    if (s != LNR_OK) return s;
+    if (!keys || !rgba) return fail(c, LNR_E_ARG, "null keys or colours");
+    if (c->soft_rel > 0.0f) return fail(c, LNR_E_STATE, "cloud shards use the hard z-buffer");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, 1, view, in, W, H, 0, &fs);
+    if (s != LNR_OK) return s;
+    enqueue_from_keys(c, ws, ws.stream, keys, nullptr, LNR_STAGE_RGBDA_RAW, c->prec);
+    cudaError_t e = cudaMemcpyAsync(rgba, ws.rgba.p, 4 * (size_t)W * H, cudaMemcpyDeviceToDevice, ws.stream);
+    if (!e) e = cudaStreamSynchronize(ws.stream);
+    if (!e) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "shard_resolve");
+    return LNR_OK;
+}
+
+// The rest of the frame from the whole cloud's keys and colours (both device, H*W): filter
+// with n_levels / fs, U-Net, out_rgb as lnr_render.
+lnr_status lnr_shard_finish(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev,
+                            float fs, const uint64_t* keys, const uint32_t* rgba, float* out, int on_device) {
+    if (!c) return LNR_E_ARG;
+    lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, true);
+    if (s != LNR_OK) return s;
+    if (!keys || !rgba || !out) return fail(c, LNR_E_ARG, "null keys, colours or output");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    if (s != LNR_OK) return s;
+    enqueue_from_keys(c, ws, ws.stream, keys, rgba, -1, c->prec);
+    const size_t bytes = 12 * (size_t)W * H;
+    cudaError_t e = cudaMemcpyAsync(out, ws.out.p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    ws.stream);
+    if (!e) e = cudaStreamSynchronize(ws.stream);
+    if (!e) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "shard_finish");
+    if (c->prec != LNR_FP32) {
+        const int w = tc_error_word();
+        if (w >= 5 && w <= 7) return fail(c, LNR_E_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait ran out)");
+        if (w) return fail(c, LNR_E_CUDA, "a tensor-core convolution could not be launched (code " + std::to_string(w) + ")");
+    }
     return LNR_OK;
 }
 

@@ -182,6 +182,9 @@ struct lnr_ctx {
     uint64_t unet_gen = 0;
     // splat collision rule: 0 = hard z-buffer, > 0 = soft with this relative depth threshold
     float soft_rel = 0.0f;
+    // cloud shard: keys carry sorted position + shard_base (the shard's first point in the
+    // whole cloud's order); the resolve colours only this shard's points
+    uint32_t shard_base = 0;
     // per-frame workspace of the synchronous calls
     lnr::Workspace ws;
     bool timing = false;
@@ -207,6 +210,10 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 void launch_clear_keys(Workspace& ws, cudaStream_t st);
 void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
+// One view from z-buffer keys (and, when rgba is non-null, resolved colours) computed
+// elsewhere: resolve, pyramid, filter, packing and (stage < 0) the U-Net.
+void enqueue_from_keys(lnr_ctx* c, Workspace& ws, cudaStream_t st, const uint64_t* keys, const uint32_t* rgba,
+                       int stage, lnr_precision prec);
 void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st);
 size_t splat_max_chunks(uint64_t npoints);  // entries per view of the splat's chunk -> first cell table
 void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,

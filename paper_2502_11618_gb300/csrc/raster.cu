@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kSplatThreads, 4) k_splat(
     const uint32_t* __restrict__ tot, const float* __restrict__ ox, const float* __restrict__ oy,
     const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ rgbs, unsigned long long* __restrict__ acc, float scale,
-    const uint32_t* __restrict__ chunk_cell, size_t max_chunks) {
+    const uint32_t* __restrict__ chunk_cell, size_t max_chunks, uint32_t pos_base) {
     // per chunk cell: camera-space origin + (sorted position of its first point - pref),
     // and pref = visible points before it (a separate array: 20 KB + 8 KB keeps five
     // blocks per SM)
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kSplatThreads, 4) k_splat(
                 if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
                 const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
                 if (!SOFT) {
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | pos[b];
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (pos[b] + pos_base);
                     atomicMin(&kv[pix], key);
                 } else {
                     const unsigned long long front = kv[pix];
@@ -333,7 +333,7 @@ __global__ void k_fill_u64(unsigned long long* __restrict__ p, size_t n) {
 __global__ void __launch_bounds__(256) k_resolve_pyramid(
     unsigned long long* __restrict__ keys, const uint32_t* __restrict__ rgbs, int W, int H, int nlev,
     float* __restrict__ depth, uint32_t* __restrict__ rgba, float* __restrict__ pyr, size_t pyr_stride,
-    unsigned long long* __restrict__ acc) {
+    unsigned long long* __restrict__ acc, uint32_t pos_base, uint32_t n_local) {
     __shared__ float s[64][65];
     __shared__ float t[32][33];
     const int view = blockIdx.z;
@@ -354,7 +354,10 @@ __global__ void __launch_bounds__(256) k_resolve_pyramid(
             uint32_t col = 0;
             if (key != kEmpty) {
                 d = __uint_as_float((uint32_t)(key >> 32));
-                col = (rgbs[(uint32_t)key] & 0x00ffffffu) | (1u << 24);
+                // a cloud shard colours only its own points; another shard's front point
+                // leaves the colour (and this buffer's A bit) zero
+                const uint32_t idx = (uint32_t)key - pos_base;
+                col = idx < n_local ? (rgbs[idx] & 0x00ffffffu) | (1u << 24) : 0u;
                 kv[q] = kEmpty;
                 if (acc) {
                     ulonglong2* a = reinterpret_cast<ulonglong2*>(acc) + view * P + q;
@@ -577,7 +580,7 @@ void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                                 ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
                                                 c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
                                                 ws.keys.as<unsigned long long>(), nullptr, nullptr, 1.0f,
-                                                ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
+                                                ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n), c->shard_base);
 }
 
 // Second pass of the soft z-buffer (after launch_splat has finished the keys).
@@ -595,7 +598,7 @@ void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                                c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
                                                ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(),
                                                ws.soft_acc.as<unsigned long long>(), scale,
-                                               ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
+                                               ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n), 0u);
 }
 
 void launch_clear_keys(Workspace& ws, cudaStream_t st) {
@@ -622,7 +625,8 @@ void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
     k_resolve_pyramid<<<g, 256, 0, st>>>(ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(), ws.W, ws.H,
                                          ws.nlev, ws.depth.as<float>(), ws.rgba.as<uint32_t>(), ws.pyr_m.as<float>(),
                                          pyramid_floats(ws.W, ws.H, ws.nlev),
-                                         c->soft_rel > 0.0f ? ws.soft_acc.as<unsigned long long>() : nullptr);
+                                         c->soft_rel > 0.0f ? ws.soft_acc.as<unsigned long long>() : nullptr, c->shard_base,
+                                         (uint32_t)c->n);
 }
 
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int kind, bool write_u0,
