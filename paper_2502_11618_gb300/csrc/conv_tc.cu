@@ -1093,6 +1093,48 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                         ++oc;
                     }
                 }
+            } else if (PAR == 0 && N == 32 && p.head_out) {
+                // fused 1x1 head on 32 channels: the next row's TMEM loads are in flight while
+                // this row's bias, ReLU, dot products and sigmoid run
+                uint32_t ua[16], ub[16];
+                if (eh < R) {
+                    tmem_ld16_async(trow + (uint32_t)(eh * 32), ua);
+                    tmem_ld16_async(trow + (uint32_t)(eh * 32 + 16), ub);
+                }
+                for (int a = eh; a < R; a += NE) {
+                    tmem_wait16(ua);
+                    tmem_wait16(ub);
+                    float f0[16], f1[16];
+                    act16(ua, 0, f0);
+                    act16(ub, 16, f1);
+                    if (a + NE < R) {
+                        tmem_ld16_async(trow + (uint32_t)((a + NE) * 32), ua);
+                        tmem_ld16_async(trow + (uint32_t)((a + NE) * 32 + 16), ub);
+                    }
+                    const int x = x0 + m, y = y0 + a;
+                    float h[4];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const float4* w4 = reinterpret_cast<const float4*>(shw + o * 32);
+                        uint64_t acc = 0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 wv = w4[j];
+                            const float* f = j < 4 ? f0 + 4 * j : f1 + 4 * (j - 4);
+                            acc = fma2(pack2(wv.x, wv.y), pack2(f[0], f[1]), acc);
+                            acc = fma2(pack2(wv.z, wv.w), pack2(f[2], f[3]), acc);
+                        }
+                        h[o] = __uint_as_float((uint32_t)acc) + __uint_as_float((uint32_t)(acc >> 32));
+                    }
+                    if (x < p.W && y < p.H) {
+                        const size_t pix = ((size_t)n * p.H + y) * p.W + x;
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            if (o >= p.head_o) break;
+                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + shw[4 * 32 + o])));
+                        }
+                    }
+                }
             } else {
                 for (int a = eh; a < NCE * R; a += NE) {
                     int x, y;
