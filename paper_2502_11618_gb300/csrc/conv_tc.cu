@@ -1573,7 +1573,7 @@ static bool halo_parity_ok(const ConvLayer& L, int P) { return P == 1 || (P >= 2
 
 // Bytes of one pipeline stage of the halo kernel for a layer at tile height R, P parity
 // classes per tile (decoder concat convs) and chunks of at most ckmax channels.
-static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, int esize = 2, int pairs = 0) {
+static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, int esize = 2) {
     const int segC[2] = {tc_c0(L), L.cin1};
     uint32_t st = 0;
     for (int sg = 0; sg < (L.cin1 ? 2 : 1); ++sg) {
@@ -1582,8 +1582,7 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
-        const int bl = halo_bload(kind, P);
-        (void)pairs;  // CTA pairs stage the same blocks (tiles of a pair share the y class)
+        const int bl = halo_bload(kind, P);  // CTA pairs stage the same blocks (a pair shares the y class)
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)bl * L.cout * pitch, 1024));
     }
     return st;
@@ -1961,7 +1960,7 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 const uint32_t sb = halo_stage_bytes(L, r, P, ck, esize);
                 if (sb * 2 > 220u * 1024u) continue;
                 // CTA pairs sharing weight stages, where weights outweigh the tile's input
-                if ((L.cin1 || N >= 128) && halo_stage_bytes(L, r, P, ck, esize, 1) * 2 <= 220u * 1024u)
+                if (L.cin1 || N >= 128)
                     for (int e : {4, 8}) {
                         TcConfig c;
                         c.mode = 1;
