@@ -133,9 +133,9 @@ def peaks():
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
 # (8 x 1080p views, BF16), from one ncu capture (profiles/traffic_multiroom20M_1080p_b8.md).
 # It describes the conv kernels as captured: reported only while their sources are unchanged.
-CONV_TRAFFIC = {"bytes_per_step": 14278.0e6,
+CONV_TRAFFIC = {"bytes_per_step": 14273.5e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "de42a98e404aa7746cc2e23691dbffd9388de75cd81b1178a50bed83c81a4959",
+                           "e37f96447c56d76f6ca80daff1607e70d914bb082cda77f3a413e1d32bcdcd4d",
                            "paper_2502_11618_gb300/csrc/unet.cu":
                            "13b937af77c5fc6470bc1d39ff3927d6aec657cd515c46df58d18f73c86ae004"}}
 
