@@ -197,16 +197,17 @@ lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
 
 /* Calibrate the FP8 (E4M3) U-Net on one view (after set_unet): the view is rendered with
  * the BF16 U-Net, the largest magnitude of every convolution's output sets that tensor's
- * static scale (8 x amax / 448: headroom for views with larger activations), and E4M3 weights with per-output-channel scales are built
- * with the input scales folded in; accumulation stays FP32 (the paper states no precision;
- * SURVEY precision pattern).  Afterwards lnr_set_precision(LNR_FP8) is allowed.  Arguments
+ * static scale (8 x amax / 448: headroom for views with larger activations), and E4M3
+ * weights with per-output-channel scales are built with the input scales folded in;
+ * accumulation stays FP32 (the paper states no precision; reduced precision is this
+ * library's addition).  Afterwards lnr_set_precision(LNR_FP8) is allowed.  Arguments
  * as lnr_render.  Errors: as lnr_render; LNR_E_ARG when a channel count of the net is not a
  * multiple of 32. */
 lnr_status lnr_calibrate(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
                          int H, int n_levels, float fs);
 
-/* Autotune the tensor-core U-Net for batches of `batch` views at W x H (SURVEY-listed
- * batching pattern; the paper has no counterpart): for every convolution, every valid
+/* Autotune the tensor-core U-Net for batches of `batch` views at W x H (part of this
+ * library's batching; the paper has no counterpart): for every convolution, every valid
  * kernel configuration (generic kernel; halo kernel over tile heights, parity classes per
  * tile and K-chunk widths) is timed on the device and the fastest is kept for that layer
  * resolution; later renders and served batches at that resolution use it.  Runs on the

@@ -587,7 +587,7 @@ lnr_status lnr_set_unet(lnr_ctx* c, const lnr_unet_desc* d, const float* w, size
     c->unet_gen++;
     if ((prec != LNR_FP32 && !tc_available()) || (prec != LNR_FP32 && L < 2)) {
         c->prec = LNR_FP32;
-        return fail(c, LNR_E_ARG, "precision not available for this net in this build");
+        return fail(c, LNR_E_ARG, "precision not available for this net");
     }
     if (prec == LNR_FP8) {  // E4M3 needs calibrated activation scales first
         c->prec = LNR_BF16;
@@ -612,7 +612,7 @@ lnr_status lnr_set_precision(lnr_ctx* c, lnr_precision prec) {
     if (!c->unet_ok) return fail(c, LNR_E_STATE, "set_precision before set_unet");
     if (prec < LNR_FP32 || prec > LNR_FP8) return fail(c, LNR_E_ARG, "bad precision");
     if ((prec != LNR_FP32 && !tc_available()) || (prec != LNR_FP32 && c->unet.levels < 2))
-        return fail(c, LNR_E_ARG, "precision not available for this net in this build");
+        return fail(c, LNR_E_ARG, "precision not available for this net");
     if (prec == LNR_FP8 && !c->unet.fp8_ready) return fail(c, LNR_E_STATE, "FP8 needs lnr_calibrate first");
     c->prec = prec;
     return LNR_OK;
@@ -736,7 +736,7 @@ lnr_status lnr_calibrate(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics*
     if (!c) return LNR_E_ARG;
     lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, true);
     if (s != LNR_OK) return s;
-    if (c->prec == LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "no tensor-core path in this build");
+    if (c->prec == LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "no tensor-core path in this library");
     for (const auto& L : c->unet.convs)
         if (L.cout < 32 || (L.cin0 != 5 && L.cin0 % 32) || L.cin1 % 32)
             return fail(c, LNR_E_ARG, "FP8 needs every U-Net channel count to be a multiple of 32");
