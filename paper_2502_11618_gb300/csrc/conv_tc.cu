@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
 // of R rows and its horizontal neighbour is the adjacent lane.
 
 constexpr int kHaloW = 130;  // staged pixels per halo row
+constexpr int kHaloMaxN = 256;  // output channels of one halo-kernel launch, at most
 
 struct HSeg {
     CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {ck, 130, rows, 1}; kind 1: 5-D, box {ck, 1, 130, rows, 1}
@@ -466,14 +467,10 @@ struct HParams {
     int tiles_x, tiles_y, ntiles;
     int stages;
     uint32_t stage_bytes, tmem_cols, idesc;
-    const float* bias;
-    const float* cscale;        // per-output-channel accumulator scale (FP8 operands), or null
     void* out;                  // NHWC output, BF16 or (out_fp8) E4M3
     void* pool_out;             // 2x2 max-pooled output, same type, or null
     int out_fp8, pool_fp8;      // output / pooled output stored as E4M3 (else BF16)
     float inv_out;              // E4M3 output: value * inv_out is stored
-    const float* head_w;
-    const float* head_b;
     float* head_out;
     int head_o;
     int* err;
@@ -490,6 +487,13 @@ struct HParams {
     int ost_nbuf;                                   // staging buffers per warp (1 or 2, used in turn)
     uint32_t ost_off, ost_warp, ost_unit, ost_row, ost_pool;  // offset, bytes per warp, per buffer, row part, pool part
     uint32_t orow_b, omask, prow_b, pmask;
+    // Per-output-channel epilogue constants, read through the constant cache (the kernel's
+    // parameter bank) rather than shared memory, whose bandwidth the MMAs' operand reads
+    // already use up: bias, accumulator scale (E4M3 operands, else 1), and the fused head's
+    // weights [4][N] (zero past head_o) followed by its 4 biases.
+    alignas(16) float cbias[kHaloMaxN];
+    alignas(16) float cscale[kHaloMaxN];
+    alignas(16) float chead[4 * kHaloMaxN + 4];
 };
 
 // 3-D box delivered to the same shared-memory offset (and barrier) of every CTA in `mask`.
@@ -781,10 +785,6 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
     const uint32_t drain = bars + 8u * (2 * S + 4);
     const uint32_t tslot = bars + 8u * (2 * S + 5);
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
-    // per-channel epilogue constants, 16-byte aligned for float4 reads (N is a multiple of 16)
-    float* sbias = reinterpret_cast<float*>(gbase + ((tslot - base + 8 + 15) & ~15u));
-    float* sscale = sbias + p.N;          // accumulator scale per output channel (E4M3 operands)
-    float* shw = sscale + p.N;            // head weights [4][N] (zero past head_o), then 4 head biases
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
     if (threadIdx.x == 0) {
@@ -800,15 +800,6 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         *flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < N; i += kHaloThreads) {
-        sbias[i] = p.bias[i];
-        sscale[i] = p.cscale ? p.cscale[i] : 1.0f;
-    }
-    if (p.head_out)
-        for (int i = threadIdx.x; i < 4 * (N + 1); i += kHaloThreads) {
-            const int o = i < 4 * N ? i / N : i - 4 * N;
-            shw[i] = o >= p.head_o ? 0.f : i < 4 * N ? p.head_w[i] : p.head_b[o];
-        }
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
@@ -955,8 +946,8 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         const bool pool = p.pool_out != nullptr;
         // bias (+ per-channel scale of E4M3 operands) and ReLU of 16 accumulator columns
         auto act16 = [&](const uint32_t (&u)[16], int c, float (&f)[16]) {
-            const float4* b4 = reinterpret_cast<const float4*>(sbias + c);
-            const float4* s4 = reinterpret_cast<const float4*>(sscale + c);
+            const float4* b4 = reinterpret_cast<const float4*>(p.cbias + c);
+            const float4* s4 = reinterpret_cast<const float4*>(p.cscale + c);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float4 bv = b4[j];
@@ -1115,7 +1106,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                     float h[4];
 #pragma unroll
                     for (int o = 0; o < 4; ++o) {
-                        const float4* w4 = reinterpret_cast<const float4*>(shw + o * 32);
+                        const float4* w4 = reinterpret_cast<const float4*>(p.chead + o * 32);
                         uint64_t acc = 0;
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
@@ -1131,7 +1122,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
 #pragma unroll
                         for (int o = 0; o < 4; ++o) {
                             if (o >= p.head_o) break;
-                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + shw[4 * 32 + o])));
+                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + p.chead[4 * 32 + o])));
                         }
                     }
                 }
@@ -1199,7 +1190,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                             // accumulated with packed FP32x2 fused multiply-adds
 #pragma unroll
                             for (int o = 0; o < 4; ++o) {
-                                const float4* w4 = reinterpret_cast<const float4*>(shw + o * N + c0);
+                                const float4* w4 = reinterpret_cast<const float4*>(p.chead + o * N + c0);
                                 uint64_t acc = 0;  // (0.f, 0.f)
 #pragma unroll
                                 for (int j = 0; j < 8; ++j) {
@@ -1228,7 +1219,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
 #pragma unroll
                         for (int o = 0; o < 4; ++o) {
                             if (o >= p.head_o) break;
-                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + shw[4 * N + o])));
+                            p.head_out[pix * p.head_o + o] = __frcp_rn(1.0f + __expf(-(h[o] + p.chead[4 * N + o])));
                         }
                     }
                     if (p.ostage) {  // the row leaves by TMA (clipped at the image edges)
@@ -1561,6 +1552,7 @@ cudaError_t tc_prepare_fp8(ConvLayer& L) {
     L.wscale8 = nullptr;
     if ((e = cudaMalloc(&L.wscale8, 4 * N)) != cudaSuccess) return e;
     L.fp8 = true;
+    L.wscale8_h = sw;
     return cudaMemcpy(L.wscale8, sw.data(), 4 * N, cudaMemcpyHostToDevice);
 }
 
@@ -1633,13 +1625,16 @@ static uint32_t halo_ostage_warp(int N, bool pool, uint32_t eo, uint32_t ep) {
 struct HaloTypes {
     bool in8 = false, out8 = false, pool8 = false;
     float inv_out = 1.f;
-    const float* cscale = nullptr;
+    const float* cscale = nullptr;  // host, per-output-channel accumulator scale (E4M3 operands), or null
 };
 
+// head_wh, head_bh: host copies of the fused head's weights [head_o][N] and biases.
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
-                  const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o, int R,
+                  const float* head_wh, const float* head_bh, float* head_out, int B, int W, int H, int head_o, int R,
                   int P, int ckmax, int O, int E, int pairs, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
     const int esize = ty.in8 ? 1 : 2;
+    if (L.cout > kHaloMaxN || (int)L.bf.size() < L.cout || (head_out && (head_o > 4 || !head_wh || !head_bh)))
+        return false;
     if (ty.in8 && ckmax < 32) return false;
     const void* whp = ty.in8 ? L.wh8[ckmax == 32 ? 0 : ckmax == 64 ? 1 : 2] : L.wh[ck_index(ckmax)];
     if (!whp) return false;
@@ -1790,20 +1785,24 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     // D = FP32; operands BF16 (format 1, kind::f16) or E4M3 (format 0, kind::f8f6f4)
     p.idesc = (1u << 4) | (ty.in8 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(N >> 3) << 17) |
               ((uint32_t)(128 >> 4) << 24);
-    p.bias = L.b32;
-    p.cscale = ty.cscale;
+    for (int i = 0; i < N; ++i) {
+        p.cbias[i] = L.bf[i];
+        p.cscale[i] = ty.cscale ? ty.cscale[i] : 1.0f;
+    }
+    if (head_out)
+        for (int o = 0; o < head_o; ++o) {
+            for (int i = 0; i < N; ++i) p.chead[o * N + i] = head_wh[o * N + i];
+            p.chead[4 * N + o] = head_bh[o];
+        }
     p.out = out;
     p.pool_out = pool_out;
     p.out_fp8 = ty.out8;
     p.pool_fp8 = ty.pool8;
     p.inv_out = ty.inv_out;
-    p.head_w = head_w;
-    p.head_b = head_b;
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
-    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16 +
-                        4 * (size_t)(2 * N + (head_out ? 4 * (N + 1) : 0));
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16;
     // CTA pairs step through padded tile counts: with 2 parity classes the (position, class)
     // tiles pair two positions of one class, 4 * ceil(positions / 2) in all; otherwise the
     // count rounded up to even
@@ -1868,8 +1867,8 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
 }
 
 void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
-             const float* head_w, const float* head_b, float* head_out, int B, int W, int H, int head_o,
-             cudaStream_t st, const TcConfig* force) {
+             const float* head_w, const float* head_b, const float* head_wh, const float* head_bh, float* head_out, int B,
+             int W, int H, int head_o, cudaStream_t st, const TcConfig* force) {
     tc_init();
     static const int forced = [] {
         const char* e = getenv("LNR_CONV_KERNEL");
@@ -1882,7 +1881,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
         ty.out8 = head_out == nullptr && !L.out_bf16;
         ty.pool8 = !L.pool_bf16;
         ty.inv_out = 1.0f / L.out_scale;
-        ty.cscale = L.fp8 ? L.wscale8 : nullptr;
+        ty.cscale = L.fp8 ? L.wscale8_h.data() : nullptr;
     }
     TcConfig cfg;
     const auto& table = fp8 ? L.tuned8 : L.tuned;
@@ -1908,7 +1907,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
                 return e && atoi(e) == 1;
             }();
             if (pairs &&
-                tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, 0, 8, 1, st, ty))
+                tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, 0, 8, 1, st, ty))
                 return;
             // LNR_CONV_TMA_STORE=0: direct stores; =1: one staging buffer per warp
             static const int tma_store = [] {
@@ -1917,11 +1916,11 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             }();
             if (tma_store > 0)
                 for (int nbuf = std::min(tma_store, 2); nbuf >= 1; --nbuf)
-                    if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, nbuf,
+                    if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, nbuf,
                                      8, 0, st, ty))
                         return;
         }
-        if (tc_conv_halo(L, src0, src1, out, pool_out, head_w, head_b, head_out, B, W, H, head_o, R, P, CK, cfg.O,
+        if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, cfg.O,
                          cfg.mode == 0 ? 8 : cfg.E, cfg.mode == 0 ? 0 : cfg.C, st, ty))
             return;
         if (fp8) {  // no fallback for FP8: record and skip

@@ -70,6 +70,7 @@ struct ConvLayer {
     float out_scale = 1.f;
     void* wh8[3] = {nullptr, nullptr, nullptr};
     float* wscale8 = nullptr;
+    std::vector<float> wscale8_h;  // host copy of wscale8
     float* wscale = nullptr;  // device, per-output-channel dequant scale (fp8), else null
     std::vector<float> wf;  // host FP32 OIHW after batch-norm folding
     std::vector<float> bf;
@@ -248,8 +249,8 @@ int unet_in_kind(lnr_precision p);
 // conv_tc.cu
 bool tc_available();
 cudaError_t tc_prepare_layer(ConvLayer& L, lnr_precision p);
-void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out,
-             void* pool_out, const float* head_w, const float* head_b, float* head_out, int B,
+void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* src1, void* out, void* pool_out,
+             const float* head_w, const float* head_b, const float* head_wh, const float* head_bh, float* head_out, int B,
              int W, int H, int head_o, cudaStream_t st, const TcConfig* force = nullptr);
 std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision p);
 cudaError_t tc_prepare_fp8(ConvLayer& L);

@@ -205,8 +205,10 @@ struct ConvCall {
     const void* src1;
     void* out;
     void* pool;
-    const float* head_w;
+    const float* head_w;   // device
     const float* head_b;
+    const float* head_wh;  // host copies
+    const float* head_bh;
     float* head_out;
     int W, H;
 };
@@ -223,8 +225,8 @@ static std::vector<ConvCall> unet_plan(const Unet& u, Workspace& ws, lnr_precisi
         void* t = ws.act[slot(l, 0)].p;
         void* s = ws.act[slot(l, 1)].p;
         void* pl = (l < L - 1) ? ws.act[slot(l, 2)].p : nullptr;
-        calls.push_back({ci, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, W, H});
-        calls.push_back({ci + 1, t, nullptr, s, pl, nullptr, nullptr, nullptr, W, H});
+        calls.push_back({ci, x, nullptr, t, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, W, H});
+        calls.push_back({ci + 1, t, nullptr, s, pl, nullptr, nullptr, nullptr, nullptr, nullptr, W, H});
         ci += 2;
         x = pl;
     }
@@ -234,9 +236,10 @@ static std::vector<ConvCall> unet_plan(const Unet& u, Workspace& ws, lnr_precisi
         void* t = ws.act[slot(l, 0)].p;
         void* d = ws.act[slot(l, 3)].p;
         const void* skip = ws.act[slot(l, 1)].p;
-        calls.push_back({ci, skip, deep, t, nullptr, nullptr, nullptr, nullptr, W, H});
+        calls.push_back({ci, skip, deep, t, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, W, H});
         const bool fuse_head = (l == 0) && p != LNR_FP32;
         calls.push_back({ci + 1, t, nullptr, d, nullptr, fuse_head ? u.head_w : nullptr, fuse_head ? u.head_b : nullptr,
+                         fuse_head ? u.head_wh.data() : nullptr, fuse_head ? u.head_bh.data() : nullptr,
                          fuse_head ? out : nullptr, W, H});
         ci += 2;
         deep = d;
@@ -250,7 +253,8 @@ static void run_call(const Unet& u, const ConvCall& k, Workspace& ws, lnr_precis
     if (p == LNR_FP32)
         conv_f32(L, (const float*)k.src0, (const float*)k.src1, (float*)k.out, (float*)k.pool, ws.B, k.W, k.H, st);
     else
-        tc_conv(L, p, k.src0, k.src1, k.out, k.pool, k.head_w, k.head_b, k.head_out, ws.B, k.W, k.H, u.out_ch, st, force);
+        tc_conv(L, p, k.src0, k.src1, k.out, k.pool, k.head_w, k.head_b, k.head_wh, k.head_bh, k.head_out, ws.B, k.W, k.H,
+                u.out_ch, st, force);
 }
 
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
