@@ -38,14 +38,17 @@ namespace lnr {
 namespace {
 
 constexpr int kThreads = 192;
-// halo kernel: producer warp, kMmaWarps MMA-issuing warps, EPI (4 or 8) epilogue warps.  One thread
-// issues about one tcgen05.mma per ~120 cycles whatever N is, so small-N convolutions need
-// several issuing threads; each owns disjoint accumulators.
+// halo kernel: producer warp, MMA-issuing warps (kMmaWarps for the decoder's concat convs,
+// whose tiles hold up to four independent units; two for standard tiles, whose rows split
+// between two issuers), then EPI epilogue warps.  One thread issues about one tcgen05.mma
+// per ~120 cycles whatever N is, so small-N convolutions need several issuing threads; each
+// owns disjoint accumulators.
 constexpr int kMmaWarps = 4;
-// Epilogue warps, chosen per layer: 4 (one per TMEM lane quarter; 288 threads allow about
-// 160 registers per thread) or 8 (two per quarter, 416 threads, 128 registers: more latency
-// hiding for stores and the fused head's dot products).
-__host__ __device__ constexpr int halo_threads(int epi) { return 32 * (1 + kMmaWarps + epi); }
+__host__ __device__ constexpr int halo_mma_warps(int par) { return par == 0 ? 2 : kMmaWarps; }
+// Epilogue warps, chosen per layer: 4 (one per TMEM lane quarter), 8 or, for standard tiles,
+// 12 (two or three per quarter: more latency hiding for TMEM loads, stores and the fused
+// head's dot products, at 128 registers per thread).
+__host__ __device__ constexpr int halo_threads(int par, int epi) { return 32 * (1 + halo_mma_warps(par) + epi); }
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
 
@@ -769,8 +772,8 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
 // class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
 template <int R, int PAR, bool IN8, int EPI>
-__global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid_constant__ HParams p) {
-    constexpr int kHaloThreads = halo_threads(EPI);
+__global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const __grid_constant__ HParams p) {
+    constexpr int MW = halo_mma_warps(PAR);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -883,7 +886,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         }
         if (!ok) atomicExch(p.err, 5);
         for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
-    } else if (warp >= 1 && warp <= kMmaWarps && lane == 0 && warp - 1 < p.nmma) {
+    } else if (warp >= 1 && warp <= MW && lane == 0 && warp - 1 < p.nmma) {
         // ----------------------------------------------------------------- MMA --
         // Issuer g owns work units [a_lo, a_hi] of every tile: standard tiles one output row
         // each; parity tiles one (row, y class) each, owning the accumulators of its NX x
@@ -935,13 +938,13 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
         (void)issued;
         mma_commit(drain);
         mbar_wait(drain, 0);
-    } else if (warp > kMmaWarps) {
+    } else if (warp > MW) {
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
         const int m = 32 * q + lane;
         constexpr int NE = EPI / 4;                   // warps per TMEM lane quarter
-        const int eh = (warp - kMmaWarps - 1) >> 2;  // which of them this warp is
-        const bool leader = threadIdx.x == 32 * (kMmaWarps + 1);
+        const int eh = (warp - MW - 1) >> 2;  // which of them this warp is
+        const bool leader = threadIdx.x == 32 * (MW + 1);
         const int Wh = p.W >> 1, Hh = p.H >> 1;
         const bool pool = p.pool_out != nullptr;
         // bias (+ per-channel scale of E4M3 operands) and ReLU of 16 accumulator columns
@@ -988,7 +991,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                 for (int r = 2 * eh; r < R; r += 2 * NE) {
                     const int x = x0 + m, y = y0 + r;
                     const bool v0 = x < p.W && y < p.H, v1 = x < p.W && y + 1 < p.H;
-                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp +
+                    const uint32_t wb = stg + (uint32_t)(warp - MW - 1) * p.ost_warp +
                                         (uint32_t)(oc % p.ost_nbuf) * p.ost_unit;
                     if (p.ostage) {  // the store that last used this staging buffer has read it
                         if (lane == 0) {
@@ -1146,7 +1149,7 @@ __global__ void __launch_bounds__(halo_threads(EPI), 1) k_conv_halo(const __grid
                     }
                     const size_t pix = ((size_t)n * p.H + y) * p.W + x;
                     float h[4] = {0.f, 0.f, 0.f, 0.f};
-                    const uint32_t wb = stg + (uint32_t)(warp - kMmaWarps - 1) * p.ost_warp +
+                    const uint32_t wb = stg + (uint32_t)(warp - MW - 1) * p.ost_warp +
                                         (uint32_t)(oc % p.ost_nbuf) * p.ost_unit;
                     if (p.ostage) {  // the store that last used this staging buffer has read it
                         if (lane == 0) {
@@ -1724,7 +1727,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.ntiles = B * p.tiles_y * p.tiles_x;
     }
     p.stage_bytes = stage;
-    const int epi = E == 4 ? 4 : 8;  // epilogue warps
+    const int epi = E == 4 ? 4 : (E == 12 && P == 0) ? 12 : 8;  // epilogue warps (12: standard tiles only)
     // epilogue stores through staging + TMA (no fused head: its outputs are per-pixel floats)
     uint32_t stg_total = 0;
     if (O) {
@@ -1839,17 +1842,17 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         constexpr int PP = decltype(par)::value, EE = decltype(ep)::value;
         if (ty.in8) {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, true, EE>, halo_threads(EE)); break;
-                case 2: launch(k_conv_halo<2, PP, true, EE>, halo_threads(EE)); break;
-                case 4: launch(k_conv_halo<4, PP, true, EE>, halo_threads(EE)); break;
-                default: launch(k_conv_halo<8, PP, true, EE>, halo_threads(EE)); break;
+                case 1: launch(k_conv_halo<1, PP, true, EE>, halo_threads(PP, EE)); break;
+                case 2: launch(k_conv_halo<2, PP, true, EE>, halo_threads(PP, EE)); break;
+                case 4: launch(k_conv_halo<4, PP, true, EE>, halo_threads(PP, EE)); break;
+                default: launch(k_conv_halo<8, PP, true, EE>, halo_threads(PP, EE)); break;
             }
         } else {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, false, EE>, halo_threads(EE)); break;
-                case 2: launch(k_conv_halo<2, PP, false, EE>, halo_threads(EE)); break;
-                case 4: launch(k_conv_halo<4, PP, false, EE>, halo_threads(EE)); break;
-                default: launch(k_conv_halo<8, PP, false, EE>, halo_threads(EE)); break;
+                case 1: launch(k_conv_halo<1, PP, false, EE>, halo_threads(PP, EE)); break;
+                case 2: launch(k_conv_halo<2, PP, false, EE>, halo_threads(PP, EE)); break;
+                case 4: launch(k_conv_halo<4, PP, false, EE>, halo_threads(PP, EE)); break;
+                default: launch(k_conv_halo<8, PP, false, EE>, halo_threads(PP, EE)); break;
             }
         }
     };
@@ -1858,7 +1861,10 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         else pick4(par, std::integral_constant<int, 4>{});
     };
     switch (P) {
-        case 0: pick(std::integral_constant<int, 0>{}); break;
+        case 0:
+            if (epi == 12) pick4(std::integral_constant<int, 0>{}, std::integral_constant<int, 12>{});
+            else pick(std::integral_constant<int, 0>{});
+            break;
         case 1: pick(std::integral_constant<int, 1>{}); break;
         case 2: pick(std::integral_constant<int, 2>{}); break;
         default: pick(std::integral_constant<int, 4>{}); break;
@@ -1873,6 +1879,13 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     static const int forced = [] {
         const char* e = getenv("LNR_CONV_KERNEL");
         return (e && !strcmp(e, "generic")) ? 2 : (e && !strcmp(e, "halo")) ? 3 : 0;
+    }();
+    // LNR_CONV_EPI=4|8|12: epilogue warps of the untuned halo kernel (default 8; 12 applies
+    // to standard tiles, the concat convs keep 8)
+    static const int epi = [] {
+        const char* e = getenv("LNR_CONV_EPI");
+        const int v = e ? atoi(e) : 8;
+        return v == 4 || v == 12 ? v : 8;
     }();
     const bool fp8 = prec == LNR_FP8;
     HaloTypes ty;
@@ -1907,7 +1920,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
                 return e && atoi(e) == 1;
             }();
             if (pairs &&
-                tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, 0, 8, 1, st, ty))
+                tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, 0, epi, 1, st, ty))
                 return;
             // LNR_CONV_TMA_STORE=0: direct stores; =1: one staging buffer per warp
             static const int tma_store = [] {
@@ -1917,11 +1930,11 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             if (tma_store > 0)
                 for (int nbuf = std::min(tma_store, 2); nbuf >= 1; --nbuf)
                     if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, nbuf,
-                                     8, 0, st, ty))
+                                     epi, 0, st, ty))
                         return;
         }
         if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, cfg.O,
-                         cfg.mode == 0 ? 8 : cfg.E, cfg.mode == 0 ? 0 : cfg.C, st, ty))
+                         cfg.mode == 0 ? epi : cfg.E, cfg.mode == 0 ? 0 : cfg.C, st, ty))
             return;
         if (fp8) {  // no fallback for FP8: record and skip
             g_host_err = 8;
@@ -1970,7 +1983,8 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                         c.C = 1;
                         out.push_back(c);
                     }
-                for (int e : {4, 8}) {
+                for (int e : {4, 8, 12}) {
+                    if (e == 12 && P) continue;  // 12 epilogue warps: standard tiles only
                     TcConfig c;
                     c.mode = 1;
                     c.R = r;

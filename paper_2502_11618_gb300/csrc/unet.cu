@@ -378,6 +378,11 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const void* in = ws.act[4 * kMaxUnetLevels].p;
+    // LNR_TUNE_LOG=1: each layer's choice on stderr; =2: also every candidate's time
+    static const int log = [] {
+        const char* v = getenv("LNR_TUNE_LOG");
+        return v ? std::max(1, atoi(v)) : 0;
+    }();
     for (const ConvCall& k : unet_plan(u, ws, p, in, ws.out.as<float>())) {
         ConvLayer& L = u.convs[k.layer];
         float best = 1e30f;
@@ -391,6 +396,9 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             if (tc_error_word()) continue;  // a configuration that failed is never chosen
+            if (log >= 2)
+                fprintf(stderr, "  candidate layer %d: mode %d R %d P %d ck %d O %d E %d C %d  %.1f us\n", k.layer, cfg.mode,
+                        cfg.R, cfg.P, cfg.CK, cfg.O, cfg.E, cfg.C, 1e3 * ms / reps);
             if (ms < best) {
                 best = ms;
                 best_cfg = cfg;
@@ -398,7 +406,6 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
         }
         if (e != cudaSuccess) break;
         (p == LNR_FP8 ? L.tuned8 : L.tuned)[{k.W, k.H}] = best_cfg;
-        static const bool log = getenv("LNR_TUNE_LOG") != nullptr;
         if (log)
             fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d C %d  %.1f us\n", k.layer, k.W, k.H,
                     best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, best_cfg.C, 1e3 * best / reps);
