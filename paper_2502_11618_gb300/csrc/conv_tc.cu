@@ -851,6 +851,8 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------------ producer --
         int use = 0;
+        int st = 0;         // stage of this use (use % S, kept incrementally)
+        uint32_t ph = 1u;   // parity that the stage's empty barrier must reach
         bool ok = true;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x) {
             int n, x0, y0, px, py;
@@ -859,8 +861,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
                 for (int cc = 0; cc < s.nchunk; ++cc) {
-                    const int st = use % S;
-                    if (!mbar_wait(empty(st), ((use / S) & 1) ^ 1)) { ok = false; break; }
+                    if (!mbar_wait(empty(st), ph)) { ok = false; break; }
                     const uint32_t a_dst = base + st * p.stage_bytes;
                     mbar_expect_tx(full(st), s.bytes);
                     const int c = cc * s.ck;
@@ -881,6 +882,10 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                                   (uint16_t)3);
                     }
                     ++use;
+                    if (++st == S) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
         }
@@ -897,7 +902,9 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         q.g = warp - 1;
         q.N = (uint32_t)N;
         q.idesc = p.idesc;
-        int use = 0, tcount = 0;
+        int tcount = 0;
+        int st = 0;        // stage (use % S, kept incrementally)
+        uint32_t ph = 0u;  // parity that the stage's full barrier must reach
         bool ok = true, issued = false;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
@@ -914,8 +921,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                 const HSeg& s = p.seg[sg];
                 const int nk = (int)(s.pitch >> 5);  // one MMA per 32 bytes of K (16 BF16 or 32 E4M3)
                 for (int cc = 0; cc < s.nchunk; ++cc) {
-                    const int st = use % S;
-                    if (!mbar_wait(full(st), (use / S) & 1)) { ok = false; break; }
+                    if (!mbar_wait(full(st), ph)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
                     const uint32_t b0 = a0 + (s.b_off >> 4);
@@ -927,7 +933,10 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                     issued = true;
                     if (p.cluster) mma_commit_mc(empty(st), (uint16_t)3);  // the stage holds both CTAs' weights
                     else mma_commit(empty(st));
-                    ++use;
+                    if (++st == S) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (ok) mma_commit(tfull(b));
