@@ -133,11 +133,11 @@ def peaks():
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
 # (8 x 1080p views, BF16), from one ncu capture (profiles/traffic_multiroom20M_1080p_b8.md).
 # It describes the conv kernels as captured: reported only while their sources are unchanged.
-CONV_TRAFFIC = {"bytes_per_step": 14273.5e6,
+CONV_TRAFFIC = {"bytes_per_step": 14270.0e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "e37f96447c56d76f6ca80daff1607e70d914bb082cda77f3a413e1d32bcdcd4d",
+                           "1036279e6f5762874f9d562ab5bb67158e8674e7137931ccf9154ad6e5e5f7df",
                            "paper_2502_11618_gb300/csrc/unet.cu":
-                           "13b937af77c5fc6470bc1d39ff3927d6aec657cd515c46df58d18f73c86ae004"}}
+                           "83a0159cfb46a21621283777895b1b70de98e4ca132ce2a83de4e2c62d5aa23c"}}
 
 
 def conv_traffic():

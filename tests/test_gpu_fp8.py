@@ -62,3 +62,63 @@ def test_fp8_psnr_against_fp64(setup):
     ref = oracle.render(g, views[1], intr, W, H, 4, 1.0, w, ch)
     assert psnr(y, ref["y"]) >= FP8_PSNR
     r.set_precision("bf16")
+
+
+
+# One FP8 render of a ragged 264 x 136 frame by the untuned halo kernel, written to argv[1].
+_FP8_SCRIPT = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import synth
+import paper_2502_11618_gb300 as lnr
+s = synth.multiroom_scene(n_points=300_000)
+ch = (32, 64, 128, 256)
+w = synth.unet_weights(ch, seed=4)
+r = lnr.Renderer(0); r.load_cloud(s.xyz, s.rgb, s.scan_id); r.build_grid(0.25); r.set_unet(ch, w, "bf16")
+W, H = 264, 136
+intr = synth.intrinsics_for(W, H)
+views = synth.random_poses(s, 3, seed=9)
+r.calibrate(views[0], intr, W, H, 4, 1.0)
+r.set_precision("fp8")
+np.save(sys.argv[1], np.stack([r.render(v, intr, W, H, 4, 1.0) for v in views[1:]]))
+"""
+
+_FP8_VARIANTS = {
+    "4_epilogue_warps": dict(LNR_CONV_EPI="4"),
+    "12_epilogue_warps": dict(LNR_CONV_EPI="12"),
+    "12_epilogue_warps_direct_stores": dict(LNR_CONV_EPI="12", LNR_CONV_TMA_STORE="0"),
+    "one_staging_buffer": dict(LNR_CONV_TMA_STORE="1"),
+    "cta_pairs": dict(LNR_CONV_CLUSTER="1"),
+}
+
+
+def _fp8_render(env_extra, tmp_path, tag):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / f"{tag}.npy")
+    env = dict(os.environ, **env_extra)
+    for k in ("LNR_CONV_EPI", "LNR_CONV_TMA_STORE", "LNR_CONV_CLUSTER", "LNR_CONV_KERNEL"):
+        if k not in env_extra:
+            env.pop(k, None)
+    r = subprocess.run([sys.executable, "-c", _FP8_SCRIPT.format(root=root), out], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return np.load(out)
+
+
+@pytest.fixture(scope="module")
+def fp8_default(setup, tmp_path_factory):
+    return _fp8_render({}, tmp_path_factory.mktemp("fp8"), "default")
+
+
+@pytest.mark.parametrize("variant", list(_FP8_VARIANTS))
+def test_fp8_each_halo_variant(fp8_default, variant, tmp_path):
+    """Forcing the untuned FP8 halo kernel to 4 or 12 epilogue warps, direct or
+    single-buffered stores, or CTA pairs changes only how accumulators leave TMEM and how
+    weight stages are shared, not the arithmetic: every variant's frames equal the default
+    configuration's bit for bit, on a ragged frame size, and stay in [0, 1]."""
+    y = _fp8_render(_FP8_VARIANTS[variant], tmp_path, variant)
+    assert 0.0 <= y.min() and y.max() <= 1.0
+    assert np.array_equal(y, fp8_default)
