@@ -133,9 +133,9 @@ def peaks():
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
 # (8 x 1080p views, BF16), from one ncu capture (profiles/traffic_multiroom20M_1080p_b8.md).
 # It describes the conv kernels as captured: reported only while their sources are unchanged.
-CONV_TRAFFIC = {"bytes_per_step": 14270.0e6,
+CONV_TRAFFIC = {"bytes_per_step": 14272.9e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "1036279e6f5762874f9d562ab5bb67158e8674e7137931ccf9154ad6e5e5f7df",
+                           "5fc8698b096b8d115707aa700c31931e89f5f528fb5d9d96c379bbadd45756e6",
                            "paper_2502_11618_gb300/csrc/unet.cu":
                            "83a0159cfb46a21621283777895b1b70de98e4ca132ce2a83de4e2c62d5aa23c"}}
 
