@@ -422,22 +422,25 @@ struct UpArgs {
     float* u0;           // kept depth tap (nullable)
 };
 
+// 32 bytes to a 32-byte-aligned global address in one store (a whole L2 sector).
+__device__ __forceinline__ void st_sector(void* dst, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4,
+                                          uint32_t w5, uint32_t w6, uint32_t w7) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w0), "r"(w1), "r"(w2),
+                 "r"(w3), "r"(w4), "r"(w5), "r"(w6), "r"(w7)
+                 : "memory");
+}
+
+// One pixel of the network input (32 bytes in both layouts), written as one sector.
 __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, float r, float g, float b,
                                               float d, float a) {
     if (kind == 0) {
-        float4* p = reinterpret_cast<float4*>(static_cast<float*>(base) + q * 8);
-        p[0] = make_float4(r, g, b, d);
-        p[1] = make_float4(a, 0.f, 0.f, 0.f);
+        st_sector(static_cast<float*>(base) + q * 8, __float_as_uint(r), __float_as_uint(g), __float_as_uint(b),
+                  __float_as_uint(d), __float_as_uint(a), 0u, 0u, 0u);
     } else if (kind == 1) {
         __nv_bfloat162 v0 = __floats2bfloat162_rn(r, g), v1 = __floats2bfloat162_rn(b, d);
-        __nv_bfloat162 v2 = __floats2bfloat162_rn(a, 0.f), v3 = __floats2bfloat162_rn(0.f, 0.f);
-        uint4 u;
-        u.x = *reinterpret_cast<uint32_t*>(&v0);
-        u.y = *reinterpret_cast<uint32_t*>(&v1);
-        u.z = *reinterpret_cast<uint32_t*>(&v2);
-        u.w = *reinterpret_cast<uint32_t*>(&v3);
-        reinterpret_cast<uint4*>(base)[2 * q] = u;
-        reinterpret_cast<uint4*>(base)[2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
+        __nv_bfloat162 v2 = __floats2bfloat162_rn(a, 0.f);
+        st_sector(static_cast<uint4*>(base) + 2 * q, *reinterpret_cast<uint32_t*>(&v0), *reinterpret_cast<uint32_t*>(&v1),
+                  *reinterpret_cast<uint32_t*>(&v2), 0u, 0u, 0u, 0u, 0u);
     }
 }
 
