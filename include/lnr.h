@@ -209,8 +209,8 @@ lnr_status lnr_calibrate(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsic
 /* Autotune the tensor-core U-Net for batches of `batch` views at W x H (part of this
  * library's batching; the paper has no counterpart): for every convolution, every valid
  * kernel configuration (generic kernel; halo kernel over tile heights, parity classes per
- * tile and K-chunk widths) is timed on the device and the fastest is kept for that layer
- * resolution; later renders and served batches at that resolution use it.  Runs on the
+ * tile, K-chunk widths, epilogue warps, direct or staged stores and CTA pairs) is timed on
+ * the device and the fastest is kept for that layer resolution; later renders and served batches at that resolution use it.  Runs on the
  * context's stream and waits for it.  Needs set_unet; a no-op for the FP32 precision.
  * Errors: LNR_E_STATE before set_unet, LNR_E_ARG for sizes as lnr_render or batch outside
  * [1, 64], LNR_E_OOM / LNR_E_CUDA. */
