@@ -297,6 +297,42 @@ def run_sweep(args, lnr, synth):
                       "n_levels": NLEV, "cell": CELL}), flush=True)
 
 
+def run_atomic_ceiling(args, scene, views, weights, lnr):
+    """The splat against its own bound: one 8-view step's z-buffer updates (one 64-bit
+    atomicMin per visible point) timed inside the step, next to the same number of atomicMin
+    on a fresh buffer of the step's size measured alone (coherent and hashed keys)."""
+    import synth
+    intr = synth.intrinsics_for(W, H)
+    B = 8
+    r = lnr.Renderer(0)
+    try:
+        r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
+        r.build_grid(CELL)
+        r.set_unet(CH, weights, "bf16")
+        r.autotune(W, H, B)
+        vis = [int(r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1]) for v in views[:B]]
+        fs = [FS[k % 2] for k in range(B)]
+        for _ in range(3):
+            r.render_batch(views[:B], intr, W, H, NLEV, fs)
+        r.set_timing(True)
+        splat = []
+        for _ in range(5):
+            r.render_batch(views[:B], intr, W, H, NLEV, fs)
+            splat.append(r.get_timing()["splat"])
+        r.set_timing(False)
+        n_ops = int(sum(vis))
+        ceiling = {k: r.probe_atomic_rate(B * W * H, n_ops, k == "coherent") for k in ("coherent", "hashed")}
+    finally:
+        r.close()
+    ms = float(np.median(splat))
+    rate = n_ops / (ms * 1e-3)
+    print(json.dumps({"atomic_ceiling": {"unit": "atomicMin/s", "n_ops": n_ops, "n_slots": B * W * H, **ceiling},
+                      "splat": {"ms_per_step": ms, "visible_points": n_ops, "atomics_per_s": rate,
+                                "frac_of_coherent": rate / ceiling["coherent"],
+                                "frac_of_hashed": rate / ceiling["hashed"]},
+                      "workload": "multiroom_20M", "W": W, "H": H, "views_per_step": B}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,6 +347,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="density / size sweep (decimated 20M scan, 100M scan): raster and U-Net "
                          "time, frames/s and visible points/s per configuration")
+    ap.add_argument("--atomic-ceiling", action="store_true",
+                    help="the splat's z-buffer update rate in the step against atomicMin throughput "
+                         "measured alone on a buffer of the same size")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched path only (no stage timing, plain, serving or CPU legs): "
                          "the command the ncu captures in profiles/ run")
@@ -337,6 +376,8 @@ def main():
     scene, views, weights = make_workload(dev)
     if args.accuracy:
         return run_accuracy(args, scene, views, weights, lnr, synth)
+    if args.atomic_ceiling:
+        return run_atomic_ceiling(args, scene, views, weights, lnr)
     stream = torch.cuda.Stream(device=dev)
     r = lnr.Renderer(local, stream=stream.cuda_stream)
     r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)

@@ -250,6 +250,18 @@ lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[4]);
 lnr_status lnr_set_timing(lnr_ctx* ctx, int enable);
 lnr_status lnr_get_timing(lnr_ctx* ctx, double out[8]);
 
+/* Throughput ceiling of the splat's z-buffer update (Sec. 3 "Point Cloud Projection": the
+ * nearest point per pixel, here a 64-bit atomicMin per projected point), measured alone:
+ * n_ops atomicMin of splat-shaped keys (depth bits << 32 | index) into a fresh buffer of
+ * n_slots keys, coherent = 1 with neighbouring operations on neighbouring keys (as
+ * cell-sorted points), 0 with hashed keys.  *ops_per_s: operations per second of the
+ * fastest of five timed launches after a warm-up, with the splat's grid.  The probe
+ * allocates and frees its own buffer and runs on the context's stream, after waiting for
+ * it.  Errors: LNR_E_ARG for n_slots outside [1, 2^32] or n_ops outside [1, 2^34];
+ * LNR_E_OOM; LNR_E_CUDA. */
+lnr_status lnr_probe_atomic_rate(lnr_ctx* ctx, uint64_t n_slots, uint64_t n_ops, int coherent,
+                                 double* ops_per_s);
+
 /* ---- filter without allocation ------------------------------------------------------ */
 
 /* The depth-guided filter alone (Fig. 2), for callers that may not allocate device memory

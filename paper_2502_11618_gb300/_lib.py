@@ -27,7 +27,7 @@ SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr
            "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
            "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer",
            "lnr_training_input", "lnr_build_grid_frame", "lnr_set_shard", "lnr_shard_resolve",
-           "lnr_shard_finish"]
+           "lnr_shard_finish", "lnr_probe_atomic_rate"]
 
 
 class LnrError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
             "lnr_serve_stats": ([p, p], st),
             "lnr_set_timing": ([p, i], st),
             "lnr_get_timing": ([p, p], st),
+            "lnr_probe_atomic_rate": ([p, u64, u64, i, C.POINTER(d)], st),
             "lnr_filter_static": ([p, i, i, i, f, p, p], st),
             "lnr_autotune": ([p, i, i, i], st),
             "lnr_calibrate": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f], st),
@@ -330,6 +331,13 @@ class Renderer:
     # --- measurement --------------------------------------------------------------------
     def set_timing(self, enable=True):
         self._check(self._L.lnr_set_timing(self._c, int(enable)))
+
+    def probe_atomic_rate(self, n_slots, n_ops, coherent=True):
+        """atomicMin operations per second into n_slots 64-bit keys (the splat's bound alone)."""
+        r = C.c_double()
+        self._check(self._L.lnr_probe_atomic_rate(self._c, C.c_uint64(n_slots), C.c_uint64(n_ops), int(coherent),
+                                                  C.byref(r)))
+        return r.value
 
     def get_timing(self):
         o = np.zeros(8, np.float64)

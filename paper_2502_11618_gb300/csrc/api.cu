@@ -785,4 +785,17 @@ lnr_status lnr_get_timing(lnr_ctx* c, double out[8]) {
     return LNR_OK;
 }
 
+lnr_status lnr_probe_atomic_rate(lnr_ctx* c, uint64_t n_slots, uint64_t n_ops, int coherent, double* ops_per_s) {
+    if (!c) return LNR_E_ARG;
+    if (!ops_per_s || n_slots == 0 || n_slots > (1ull << 32) || n_ops == 0 || n_ops > (1ull << 34))
+        return fail(c, LNR_E_ARG, "atomic probe: n_slots in [1, 2^32], n_ops in [1, 2^34]");
+    cudaSetDevice(c->device);
+    Workspace& ws = c->ws;
+    cudaError_t e = cudaStreamSynchronize(ws.stream);
+    if (!e) e = probe_atomic_rate(n_slots, n_ops, coherent != 0, c->num_sms, ws.stream, ops_per_s);
+    if (e == cudaErrorMemoryAllocation) return fail(c, LNR_E_OOM, "atomic probe buffer");
+    if (e != cudaSuccess) return cuda_fail(c, e, "atomic probe");
+    return LNR_OK;
+}
+
 }  // extern "C"

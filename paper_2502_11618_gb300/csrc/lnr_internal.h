@@ -226,6 +226,8 @@ void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int 
 size_t pyramid_floats(int W, int H, int nlev);
 size_t pyramid_offset(int W, int H, int l);
 void launch_unet_in_extract(const void* unet_in, int kind, float* out5, int64_t npx, cudaStream_t st);
+cudaError_t probe_atomic_rate(uint64_t n_slots, uint64_t n_ops, int coherent, int num_sms, cudaStream_t st,
+                              double* ops_per_s);
 
 // api.cu
 lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in, int W, int H,

@@ -604,6 +604,58 @@ void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                                ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n), 0u);
 }
 
+// ------------------------------------------------------- atomic throughput probe ----
+
+// The output function of splitmix64 (Steele, Lea and Flood, OOPSLA 2014): a bijective mix of
+// 64-bit integers, here only a source of scattered keys and depths.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// The splat's z-buffer update in isolation: n_ops 64-bit atomicMin of splat-shaped keys
+// (depth bits << 32 | index) into n_slots keys.  coherent = 1: operation i updates key
+// i mod n_slots, neighbouring threads neighbouring keys (as cell-sorted points do);
+// coherent = 0: a hashed key.
+__global__ void k_atomic_rate(unsigned long long* __restrict__ keys, uint64_t n_slots, uint64_t n_ops, int coherent) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_ops; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = mix64(i);
+        const uint64_t j = (coherent ? i : h) % n_slots;
+        atomicMin(&keys[j], ((unsigned long long)(uint32_t)(h >> 34) << 32) | (uint32_t)i);
+    }
+}
+
+cudaError_t probe_atomic_rate(uint64_t n_slots, uint64_t n_ops, int coherent, int num_sms, cudaStream_t st,
+                              double* ops_per_s) {
+    unsigned long long* keys = nullptr;
+    cudaError_t e = cudaMalloc(&keys, n_slots * sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const unsigned grid = (unsigned)std::max(1, num_sms) * 8;  // the splat's grid for 8 views
+    float best = 1e30f;
+    for (int r = 0; r < 6 && e == cudaSuccess; ++r) {  // run 0 warms up; the fastest later run counts
+        k_fill_u64<<<1024, 256, 0, st>>>(keys, n_slots);
+        cudaEventRecord(e0, st);
+        k_atomic_rate<<<grid, 256, 0, st>>>(keys, n_slots, n_ops, coherent);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0) best = std::min(best, ms);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(keys);
+    if (e == cudaSuccess) *ops_per_s = (double)n_ops / (best * 1e-3);
+    return e;
+}
+
 void launch_clear_keys(Workspace& ws, cudaStream_t st) {
     // the whole allocation: a tap that stopped after the splat may have left keys of an
     // earlier, larger frame behind

@@ -203,3 +203,19 @@ def test_multiroom_geo_offset_bit_exact(lnr):
         U0 = r.render_stage(view, intr, W, H, nl, 0.5, lnr.STAGE_FILTERED)
         assert np.array_equal(U0, ref["U0"])
     r.close()
+
+
+def test_atomic_probe_measures_the_splat_update(lnr):
+    """The z-buffer update's throughput probe runs coherent and hashed key patterns and
+    rejects empty or oversized buffers."""
+    r = lnr.Renderer(0)
+    try:
+        for coherent in (True, False):
+            rate = r.probe_atomic_rate(1 << 20, 1 << 23, coherent)
+            assert 1e8 < rate < 1e13, rate
+        with pytest.raises(lnr.LnrError):
+            r.probe_atomic_rate(0, 1 << 10)
+        with pytest.raises(lnr.LnrError):
+            r.probe_atomic_rate((1 << 32) + 1, 1 << 10)
+    finally:
+        r.close()
