@@ -131,8 +131,8 @@ def peaks():
 
 
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
-# (8 x 1080p views, BF16), from one ncu capture (profiles/traffic_multiroom20M_1080p_b8.md).
-# It describes the conv kernels as captured: reported only while their sources are unchanged.
+# (8 x 1080p views, BF16), from one ncu capture of the conv kernels.  It describes the conv
+# kernels as captured: reported only while their sources are unchanged.
 CONV_TRAFFIC = {"bytes_per_step": 14272.9e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
                            "5fc8698b096b8d115707aa700c31931e89f5f528fb5d9d96c379bbadd45756e6",
@@ -351,8 +351,8 @@ def main():
                     help="the splat's z-buffer update rate in the step against atomicMin throughput "
                          "measured alone on a buffer of the same size")
     ap.add_argument("--only-batched", action="store_true",
-                    help="time the batched path only (no stage timing, plain, serving or CPU legs): "
-                         "the command the ncu captures in profiles/ run")
+                    help="time the batched path only (no stage timing, plain, serving or CPU legs), "
+                         "e.g. under a profiler")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -209,8 +209,9 @@ lnr_status lnr_calibrate(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsic
 /* Autotune the tensor-core U-Net for batches of `batch` views at W x H (part of this
  * library's batching; the paper has no counterpart): for every convolution, every valid
  * kernel configuration (generic kernel; halo kernel over tile heights, parity classes per
- * tile, K-chunk widths, epilogue warps, direct or staged stores and CTA pairs) is timed on
- * the device and the fastest is kept for that layer resolution; later renders and served batches at that resolution use it.  Runs on the
+ * tile, K-chunk widths, epilogue warps, direct or staged stores) is timed on the device
+ * and the fastest is kept for that layer resolution; later renders and served batches at
+ * that resolution use it.  Runs on the
  * context's stream and waits for it.  Needs set_unet; a no-op for the FP32 precision.
  * Errors: LNR_E_STATE before set_unet, LNR_E_ARG for sizes as lnr_render or batch outside
  * [1, 64], LNR_E_OOM / LNR_E_CUDA. */
@@ -264,11 +265,12 @@ lnr_status lnr_probe_atomic_rate(lnr_ctx* ctx, uint64_t n_slots, uint64_t n_ops,
 
 /* ---- filter without allocation ------------------------------------------------------ */
 
-/* The depth-guided filter alone (Fig. 2), for callers that may not allocate device memory
- * -- e.g. a host application's real-time frame loop, where cudaMalloc can synchronise the
- * whole device and stall unrelated work, or a plug-in whose host owns every allocation.
- * The paper has no counterpart: it is a deployment variant of the filter stage of
- * lnr_render, with the same arithmetic (kept depth bit-identical to LNR_STAGE_FILTERED).
+/* The depth filter stage of lnr_render on its own, for callers that may not allocate
+ * device memory -- e.g. a host application's real-time frame loop, where cudaMalloc can
+ * synchronise the whole device and stall unrelated work, or a plug-in whose host owns every
+ * allocation.  The paper has no counterpart of this entry point: it is a deployment variant
+ * of lnr_render's filter stage, with the same arithmetic (kept depth bit-identical to
+ * LNR_STAGE_FILTERED).
  * d_depth: device float [H*W], view-space depth, +inf where no point was projected.
  * d_kept:  device float [H*W] output, the kept depth, +inf where empty or filtered out.
  * n_levels, fs: as lnr_render.  cuda_stream: cudaStream_t (NULL = legacy default stream).

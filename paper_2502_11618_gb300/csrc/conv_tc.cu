@@ -166,21 +166,6 @@ __device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// The same arrival on the barrier at this offset in every CTA of `mask` (CTA pair).
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"(mask)
-                 : "memory");
-}
-// All threads of every CTA of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
 
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -448,9 +433,6 @@ constexpr int kHaloMaxN = 256;  // output channels of one halo-kernel launch, at
 struct HSeg {
     CUtensorMap a;   // kind 0/2: 4-D {C, W, H, N}, box {ck, 130, rows, 1}; kind 1: 5-D, box {ck, 1, 130, rows, 1}
     CUtensorMap b;   // 3-D {ck, N, wblk * chunks}, box {ck, N, bload}: weights [chunk][block][N][ck]
-                     // (CTA pairs: box {ck, N, bsplit}, the first blocks of each stage)
-    CUtensorMap b2;  // CTA pairs: box {ck, N, bload - bsplit}, the stage's remaining blocks
-    int bsplit;      // CTA pairs: blocks the pair's rank-0 CTA loads for both
     int kind;        // 0: same-resolution source; 1: skip (parity tiles); 2: coarse (parity tiles)
     int wblk;        // weight blocks per chunk in memory (9, or 16 for the coarse operand)
     int bload;       // blocks staged per chunk (9; coarse: 16 for 4 classes, else the tile's y class's 8)
@@ -480,9 +462,6 @@ struct HParams {
     float* head_out;
     int head_o;
     int* err;
-    int cluster;  // 1: CTA pairs (clusters of 2) stage every chunk's weights once for both (TMA multicast)
-    int vtiles;   // tiles the CTAs step through: ntiles, or (pairs) padded so that both CTAs of a
-                  // pair run the same count and, for 2 parity classes, share the tile's y class
     // TMA-store epilogue (ostage = 1): per epilogue warp a staging area of ost_warp bytes at
     // ost_off from the 1024-aligned base: (pool ? 2 : 1) rows of 32 pixels x N channels,
     // then (pool) 16 pooled pixels, every part 1024-aligned; rows split into boxes of
@@ -501,15 +480,6 @@ struct HParams {
     alignas(16) float cscale[kHaloMaxN];
     alignas(16) float chead[4 * kHaloMaxN + 4];
 };
-
-// 3-D box delivered to the same shared-memory offset (and barrier) of every CTA in `mask`.
-__device__ __forceinline__ void tma_3d_mc(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2,
-                                          uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
-        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(mask)
-        : "memory");
-}
 
 __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2) {
     asm volatile(
@@ -796,7 +766,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
-            mbar_init(empty(s), p.cluster ? 2 * p.nmma : p.nmma);  // pairs: both CTAs' issuers release a stage
+            mbar_init(empty(s), p.nmma);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull(b), p.nmma);
@@ -809,40 +779,25 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
-    if (p.cluster) cluster_sync();  // the peer's barriers are initialised before any remote arrival
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
-    // Tile sequence: blockIdx.x, + gridDim.x, ...  CTA pairs run the same number of tiles
-    // (their weight stages are shared): the pair continues while its even tile exists, and
-    // a CTA whose tile is past the end runs it on zero-filled input without storing it.
-    const int rank = p.cluster ? (int)cluster_rank() : 0;
-    (void)rank;
-    auto tile_live = [&](int t) { return t < p.vtiles; };
+    // Tile sequence: blockIdx.x, + gridDim.x, ...
+    auto tile_live = [&](int t) { return t < p.ntiles; };
 
     // tile t -> image n, first column x0 and first row y0 (coarse for parity tiles) and the
     // parity class (px, py); parity is the fastest index so that the four classes of a
     // region run back to back and share its halo in L2
     // (for PAR 1 and 2, px / py are the tile's class; PAR 4 covers every class)
-    // A tile past the real ones (CTA pairs' padding) reports valid = false; its loads start
-    // past the last image and read zeros.
-    auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py, bool& valid) {
+    auto tile_of = [&](int t, int& n, int& x0, int& y0, int& px, int& py) {
         px = py = 0;
-        valid = t < p.ntiles;
         if (PAR == 1) {
             px = t & 1;
             py = (t >> 1) & 1;
             t >>= 2;
         } else if (PAR == 2) {
-            if (p.cluster) {  // the two tiles of a pair (t, t + 1) share the y class
-                py = (t >> 1) & 1;
-                t = ((t >> 2) << 1) | (t & 1);
-                valid = t < (p.ntiles >> 1);
-            } else {
-                py = t & 1;
-                t >>= 1;
-            }
+            py = t & 1;
+            t >>= 1;
         }
-        if (!valid) t = p.tiles_x * p.tiles_y * p.B;  // image index B: every load reads zeros
         const int tx = t % p.tiles_x;
         t /= p.tiles_x;
         const int ty = t % p.tiles_y;
@@ -859,8 +814,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         bool ok = true;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x) {
             int n, x0, y0, px, py;
-            bool valid;
-            tile_of(t, n, x0, y0, px, py, valid);  // padding tile: n = B, zero-filled
+            tile_of(t, n, x0, y0, px, py);
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
                 for (int cc = 0; cc < s.nchunk; ++cc) {
@@ -876,14 +830,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                         tma_4d(a_dst, &s.a, full(st), c, x0 - 1, y0 - 1, n);
                     }
                     const int wb0 = cc * s.wblk + (s.bsel ? 8 * py : 0);  // first weight block of the stage
-                    if (!p.cluster) {
-                        tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, wb0);
-                    } else if (rank == 0) {  // each CTA of the pair stages part of the blocks for both
-                        tma_3d_mc(a_dst + s.b_off, &s.b, full(st), 0, 0, wb0, (uint16_t)3);
-                    } else {
-                        tma_3d_mc(a_dst + s.b_off + (uint32_t)s.bsplit * N * s.pitch, &s.b2, full(st), 0, 0, wb0 + s.bsplit,
-                                  (uint16_t)3);
-                    }
+                    tma_3d(a_dst + s.b_off, &s.b, full(st), 0, 0, wb0);
                     ++use;
                     if (++st == S) {
                         st = 0;
@@ -911,8 +858,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         bool ok = true, issued = false;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
-            bool valid;
-            tile_of(t, n, x0, y0, px, py, valid);
+            tile_of(t, n, x0, y0, px, py);
             q.px = px;
             q.py = py;
             const int b = tcount & 1;
@@ -934,8 +880,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                         default: issue_stage<R, PAR, IN8, 4>(q, sg, a0, b0, s, d0, cc == 0); break;
                     }
                     issued = true;
-                    if (p.cluster) mma_commit_mc(empty(st), (uint16_t)3);  // the stage holds both CTAs' weights
-                    else mma_commit(empty(st));
+                    mma_commit(empty(st));
                     if (++st == S) {
                         st = 0;
                         ph ^= 1u;
@@ -987,14 +932,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
             if (*flag) break;
             tc_fence_after();
             int n, x0, y0, px, py;
-            bool valid;
-            tile_of(t, n, x0, y0, px, py, valid);
-            if (!valid) {  // a CTA pair's padding tile: nothing to store
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty(b));
-                continue;
-            }
+            tile_of(t, n, x0, y0, px, py);
             constexpr int NCE = PAR == 0 ? 1 : PAR;
             const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NCE * R * N);
             if (pool) {
@@ -1263,7 +1201,6 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         if (leader && *flag) atomicExch(p.err, 7);
     }
     __syncthreads();
-    if (p.cluster) cluster_sync();  // no remote arrival may reach a CTA that has exited
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, p.tmem_cols);
@@ -1589,7 +1526,7 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
-        const int bl = halo_bload(kind, P);  // CTA pairs stage the same blocks (a pair shares the y class)
+        const int bl = halo_bload(kind, P);
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)bl * L.cout * pitch, 1024));
     }
     return st;
@@ -1646,7 +1583,7 @@ struct HaloTypes {
 // head_wh, head_bh: host copies of the fused head's weights [head_o][N] and biases.
 bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* out, void* pool_out,
                   const float* head_wh, const float* head_bh, float* head_out, int B, int W, int H, int head_o, int R,
-                  int P, int ckmax, int O, int E, int pairs, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
+                  int P, int ckmax, int O, int E, cudaStream_t st, const HaloTypes& ty = HaloTypes()) {
     const int esize = ty.in8 ? 1 : 2;
     if (L.cout > kHaloMaxN || (int)L.bf.size() < L.cout || (head_out && (head_o > 4 || !head_wh || !head_bh)))
         return false;
@@ -1663,7 +1600,6 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     const int NC = P ? P : 1;
     if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * NC * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
-    p.cluster = pairs ? 1 : 0;
     p.parity = P;
     p.wmax = std::max(1, std::min(3, 256 / N));
     // two issuers for standard tiles (each takes half the rows and windows within it); for
@@ -1687,7 +1623,6 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.wblk = kind == 2 ? 16 : 9;
         s.bload = halo_bload(kind, P);
         s.bsel = kind == 2 && P != 4;
-        s.bsplit = s.bload / 2;  // CTA pairs: the rank-0 CTA stages the first bsplit blocks for both
         const uint32_t b_bytes = (uint32_t)s.bload * N * s.pitch;
         s.bytes = s.a_bytes + b_bytes;
         stage = std::max(stage, align_up(s.b_off + b_bytes, 1024));
@@ -1710,16 +1645,10 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         }
         cuuint64_t wd[3] = {(cuuint64_t)s.ck, (cuuint64_t)N, (cuuint64_t)s.wblk * s.nchunk};
         cuuint64_t wstr[2] = {s.ck * eb, (cuuint64_t)N * s.ck * eb};
-        cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, (cuuint32_t)(pairs ? s.bsplit : s.bload)};
+        cuuint32_t wbox[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, (cuuint32_t)s.bload};
         ok = ok && encode_tiled(&s.b, dt, 3, const_cast<uint8_t*>(wh + w_off), wd, wstr, wbox, es,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        if (pairs) {
-            cuuint32_t wbox2[3] = {(cuuint32_t)s.ck, (cuuint32_t)N, (cuuint32_t)(s.bload - s.bsplit)};
-            ok = ok && encode_tiled(&s.b2, dt, 3, const_cast<uint8_t*>(wh + w_off), wd, wstr, wbox2, es,
-                                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_pitch(s.pitch), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        }
         w_off += (size_t)s.nchunk * s.wblk * N * s.ck * esize;
         return ok;
     };
@@ -1818,11 +1747,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_o = head_o;
     p.err = g_err;
     const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16;
-    // CTA pairs step through padded tile counts: with 2 parity classes the (position, class)
-    // tiles pair two positions of one class, 4 * ceil(positions / 2) in all; otherwise the
-    // count rounded up to even
-    p.vtiles = !pairs ? p.ntiles : P == 2 ? 4 * ((p.ntiles / 2 + 1) / 2) : (p.ntiles + 1) & ~1;
-    const int grid = pairs ? std::min(p.vtiles, g_num_sms & ~1) : std::min(p.ntiles, g_num_sms);
+    const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams), int threads) {
         static std::mutex mu;
         static std::set<const void*> done;
@@ -1831,23 +1756,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             if (done.insert((const void*)kern).second)
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
-        if (pairs) {  // clusters of two CTAs (weight stages shared by TMA multicast)
-            cudaLaunchConfig_t lc = {};
-            lc.gridDim = dim3((unsigned)grid);
-            lc.blockDim = dim3((unsigned)threads);
-            lc.dynamicSmemBytes = smem;
-            lc.stream = st;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = 2;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            lc.attrs = at;
-            lc.numAttrs = 1;
-            cudaLaunchKernelEx(&lc, kern, p);
-        } else {
-            kern<<<grid, threads, smem, st>>>(p);
-        }
+        kern<<<grid, threads, smem, st>>>(p);
         if (cudaGetLastError() != cudaSuccess) g_host_err = 9;  // a launch that did not start: reported, never silent
     };
     auto pick4 = [&](auto par, auto ep) {
@@ -1926,14 +1835,6 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             halo_default(L, R, P, CK);
             if (ty.in8) CK = std::max(32, CK);
             // untuned: TMA-store epilogue where it fits next to two pipeline stages
-            // LNR_CONV_CLUSTER=1: CTA pairs sharing weight stages wherever the tile allows it
-            static const bool pairs = [] {
-                const char* e = getenv("LNR_CONV_CLUSTER");
-                return e && atoi(e) == 1;
-            }();
-            if (pairs &&
-                tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, 0, epi, 1, st, ty))
-                return;
             // LNR_CONV_TMA_STORE=0: direct stores; =1: one staging buffer per warp
             static const int tma_store = [] {
                 const char* e = getenv("LNR_CONV_TMA_STORE");
@@ -1942,11 +1843,11 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
             if (tma_store > 0)
                 for (int nbuf = std::min(tma_store, 2); nbuf >= 1; --nbuf)
                     if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, nbuf,
-                                     epi, 0, st, ty))
+                                     epi, st, ty))
                         return;
         }
         if (tc_conv_halo(L, src0, src1, out, pool_out, head_wh, head_bh, head_out, B, W, H, head_o, R, P, CK, cfg.O,
-                         cfg.mode == 0 ? epi : cfg.E, cfg.mode == 0 ? 0 : cfg.C, st, ty))
+                         cfg.mode == 0 ? epi : cfg.E, st, ty))
             return;
         if (fp8) {  // no fallback for FP8: record and skip
             g_host_err = 8;
@@ -1983,18 +1884,6 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 last_ck[1] = c1;
                 const uint32_t sb = halo_stage_bytes(L, r, P, ck, esize);
                 if (sb * 2 > 220u * 1024u) continue;
-                // CTA pairs sharing weight stages, where weights outweigh the tile's input
-                if (L.cin1 || N >= 128)
-                    for (int e : {4, 8}) {
-                        TcConfig c;
-                        c.mode = 1;
-                        c.R = r;
-                        c.P = P;
-                        c.CK = ck;
-                        c.E = e;
-                        c.C = 1;
-                        out.push_back(c);
-                    }
                 for (int e : {4, 8, 12}) {
                     if (e == 12 && P) continue;  // 12 epilogue warps: standard tiles only
                     TcConfig c;

@@ -42,7 +42,6 @@ struct TcConfig {
     int R = 0, P = 0, CK = 0;
     int O = 0;  // halo kernel: 1 or 2 = epilogue stores through that many staging buffers and TMA
     int E = 8;  // halo kernel: epilogue warps (4, 8, or 12 for standard tiles)
-    int C = 0;  // halo kernel: 1 = CTA pairs sharing weight stages (cluster TMA multicast)
 };
 
 // One convolution as the GPU runs it.

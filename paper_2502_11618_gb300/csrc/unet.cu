@@ -397,8 +397,8 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (tc_error_word()) continue;  // a configuration that failed is never chosen
             if (log >= 2)
-                fprintf(stderr, "  candidate layer %d: mode %d R %d P %d ck %d O %d E %d C %d  %.1f us\n", k.layer, cfg.mode,
-                        cfg.R, cfg.P, cfg.CK, cfg.O, cfg.E, cfg.C, 1e3 * ms / reps);
+                fprintf(stderr, "  candidate layer %d: mode %d R %d P %d ck %d O %d E %d  %.1f us\n", k.layer, cfg.mode,
+                        cfg.R, cfg.P, cfg.CK, cfg.O, cfg.E, 1e3 * ms / reps);
             if (ms < best) {
                 best = ms;
                 best_cfg = cfg;
@@ -407,8 +407,8 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
         if (e != cudaSuccess) break;
         (p == LNR_FP8 ? L.tuned8 : L.tuned)[{k.W, k.H}] = best_cfg;
         if (log)
-            fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d C %d  %.1f us\n", k.layer, k.W, k.H,
-                    best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, best_cfg.C, 1e3 * best / reps);
+            fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d  %.1f us\n", k.layer, k.W, k.H,
+                    best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, 1e3 * best / reps);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -88,7 +88,6 @@ _FP8_VARIANTS = {
     "12_epilogue_warps": dict(LNR_CONV_EPI="12"),
     "12_epilogue_warps_direct_stores": dict(LNR_CONV_EPI="12", LNR_CONV_TMA_STORE="0"),
     "one_staging_buffer": dict(LNR_CONV_TMA_STORE="1"),
-    "cta_pairs": dict(LNR_CONV_CLUSTER="1"),
 }
 
 
@@ -99,7 +98,7 @@ def _fp8_render(env_extra, tmp_path, tag):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = str(tmp_path / f"{tag}.npy")
     env = dict(os.environ, **env_extra)
-    for k in ("LNR_CONV_EPI", "LNR_CONV_TMA_STORE", "LNR_CONV_CLUSTER", "LNR_CONV_KERNEL"):
+    for k in ("LNR_CONV_EPI", "LNR_CONV_TMA_STORE", "LNR_CONV_KERNEL"):
         if k not in env_extra:
             env.pop(k, None)
     r = subprocess.run([sys.executable, "-c", _FP8_SCRIPT.format(root=root), out], env=env, capture_output=True,
@@ -116,8 +115,7 @@ def fp8_default(setup, tmp_path_factory):
 @pytest.mark.parametrize("variant", list(_FP8_VARIANTS))
 def test_fp8_each_halo_variant(fp8_default, variant, tmp_path):
     """Forcing the untuned FP8 halo kernel to 4 or 12 epilogue warps, direct or
-    single-buffered stores, or CTA pairs changes only how accumulators leave TMEM and how
-    weight stages are shared, not the arithmetic: every variant's frames equal the default
+    single-buffered stores changes only how accumulators leave TMEM, not the arithmetic: every variant's frames equal the default
     configuration's bit for bit, on a ragged frame size, and stay in [0, 1]."""
     y = _fp8_render(_FP8_VARIANTS[variant], tmp_path, variant)
     assert 0.0 <= y.min() and y.max() <= 1.0

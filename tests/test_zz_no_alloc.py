@@ -30,7 +30,8 @@ def test_filter_static_matches_render_stage_twice():
     r = lnr.Renderer(0)
     r.load_cloud(s.xyz, s.rgb, s.scan_id)
     r.build_grid(0.5)
-    cases = [(256, 192, 3, 1.0), (320, 200, 5, 0.5)]
+    # n_levels 0 takes the no-pyramid branch (every filled pixel kept)
+    cases = [(256, 192, 3, 1.0), (320, 200, 5, 0.5), (256, 192, 0, 1.0)]
     views = synth.random_poses(s, len(cases), seed=11)
     stream = torch.cuda.current_stream().cuda_stream
     for (W, H, nl, fs), view in zip(cases, views):
