@@ -166,10 +166,16 @@ def oracle_grid(scene):
     return oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
 
 
+CONFIG = {"workload": "multiroom_20M", "W": W, "H": H, "n_points": N_POINTS, "views_per_step": 8,
+          "n_levels": NLEV, "filter_strength": list(FS), "cell": CELL, "unet": list(CH)}
+
+
 def cpu_sample(g, views, weights, crop=(480, 272)):
-    """Oracle time of one 1080p frame: cull + splat + filter of a full view (one thread),
-    the FP64 U-Net on a crop scaled by pixel count to the full frame (all cores).  The
-    grid `g` is built once per cloud, outside the sample."""
+    """Oracle time of one 1080p frame, from a bounded sample: cull + splat + filter of a
+    full view (one thread) and the FP64 U-Net on a crop (all cores), scaled by pixel count
+    to the full frame.  The grid `g` is built once per cloud, outside the sample.  Returns
+    the frame-rate estimate, the sample's own wall time and the fraction of a frame's work
+    the sample did (by time)."""
     import oracle
     import synth
     intr = synth.intrinsics_for(W, H)
@@ -180,34 +186,41 @@ def cpu_sample(g, views, weights, crop=(480, 272)):
     x = ref["x"][(H - chh) // 2:(H - chh) // 2 + chh, (W - cw) // 2:(W - cw) // 2 + cw]
     t0 = time.perf_counter()
     oracle.unet(np.ascontiguousarray(x), CH, weights)
-    t_unet = (time.perf_counter() - t0) * (W * H) / (cw * chh)
+    t_crop = time.perf_counter() - t0
+    t_unet = t_crop * (W * H) / (cw * chh)
     s_per_frame = t_raster + t_unet
     return {"value": 1.0 / s_per_frame, "unit": "frames/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "sample_s": t_raster + t_crop,
+            "frames_per_sample": (t_raster + t_crop) / s_per_frame,
             "sample": (f"one 1920x1080 view: cull+splat+filter of the 20M-point scan on 1 core "
-                       f"({t_raster:.2f} s) + FP64 U-Net on a {cw}x{chh} crop scaled by pixel count "
-                       f"({t_unet:.1f} s per frame)")}
+                       f"({t_raster:.2f} s) + FP64 U-Net on a {cw}x{chh} crop ({t_crop:.2f} s), "
+                       f"scaled by pixel count to {t_unet:.1f} s per frame")}
 
 
 def run_reference(args):
+    """The oracle on the host cores, on this benchmark's workload: each step is one bounded
+    sample (a whole 1080p view through cull, splat and filter; the FP64 U-Net on a crop).
+    ms_per_step is the sample's measured wall time; value is the frame rate the samples give
+    (frames_per_step = the fraction of a frame's work one sample does)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     scene, views, weights = make_workload("cpu")
     g = oracle_grid(scene)
-    times = []
+    wall, frames = [], []
     for i in range(args.warmup + args.steps):
         r = cpu_sample(g, [views[i % len(views)]], weights)
         if i >= args.warmup:
-            times.append(1.0 / r["value"])
-    v = len(times) / sum(times)
-    cb = dict(r)
+            wall.append(r["sample_s"])
+            frames.append(r["frames_per_sample"])
+    v = sum(frames) / sum(wall)
+    cb = {k: r[k] for k in ("unit", "cores", "kind", "sample")}
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(wall) / len(wall),
+            "frames_per_step": sum(frames) / len(frames),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "multiroom_20M", "W": W, "H": H, "n_points": N_POINTS,
-                                             "n_levels": NLEV, "cell": CELL, "unet": list(CH)},
+            "data": "synthetic", "config": dict(CONFIG),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -222,7 +235,7 @@ def run_accuracy(args, scene, views, weights, lnr, synth):
     r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
     r.build_grid(CELL)
     r.set_unet(CH, weights, "bf16")
-    r.calibrate(views[0], intr, W, H, NLEV, FS[0])
+    r.calibrate(synth.random_poses(scene, 4, seed=77), intr, W, H, NLEV, 1.0)
     g = oracle.build_grid(scene.xyz, scene.rgb, scene.scan_id, CELL)
     res = {p: {"max_abs": 0.0, "min_psnr": 1e9} for p in ("fp32", "bf16", "fp8")}
     vs = synth.random_poses(scene, args.accuracy, seed=2)
@@ -333,6 +346,197 @@ def run_atomic_ceiling(args, scene, views, weights, lnr):
                       "workload": "multiroom_20M", "W": W, "H": H, "views_per_step": B}), flush=True)
 
 
+def spawn_replicas(n):
+    """Re-run this command as n ranks, one GPU each (torch.distributed.run on 127.0.0.1);
+    returns the launcher's exit status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def run_replica_selftest(args):
+    """The replica plumbing without a GPU: every rank (gloo) reports a step time of its own,
+    and rank 0 prints the whole-job aggregate (frames of all ranks / slowest rank's time)."""
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    tot_ms = 10.0 * (1 + rank)
+    value, slowest = aggregate(tot_ms, 8, dist if world > 1 else None, "cpu")
+    if rank == 0:
+        print(json.dumps({"replica_selftest": True, "world": world, "value": value, "slowest_ms": slowest}),
+              flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def stage_roofline(stage_ms, nvis, n_px, hbm_gbs):
+    """HBM roofline of the raster stages from their algorithmic bytes: splat 12 B per
+    visible point (FP32 offsets), resolve 28 B per pixel (key read + clear, colour gather,
+    RGBDA write), filter 28 B per pixel (pyramid levels, the level-0 read and the network
+    input).  stage_ms: library stage events of one step; nvis: visible points of the step."""
+    parts = {"splat": (12.0 * nvis, stage_ms["splat"]),
+             "splat_resolve": (12.0 * nvis + 28.0 * n_px, stage_ms["splat"] + stage_ms["resolve_pyramid"]),
+             "filter": (28.0 * n_px, stage_ms["upsample_pack"])}
+    out = {}
+    for k, (b, ms) in parts.items():
+        gbs = b / (ms * 1e-3) / 1e9
+        out[k] = {"bound": "hbm", "algorithmic_bytes": b, "ms": ms, "achieved": gbs, "peak": hbm_gbs,
+                  "unit": "GB/s", "frac": gbs / hbm_gbs}
+    return out
+
+
+def percentiles(lat_ms):
+    a = np.asarray(lat_ms, np.float64)
+    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+
+
+_PINNED = {}   # (W, H) -> free page-locked result buffers, reused across serving runs
+
+
+def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, window=48):
+    """Serve `reqs` (synth.requests.Request) through lnr_submit_into / lnr_poll: at their
+    arrival times when realtime, else closed loop with at most `window` requests
+    outstanding.  Every result is copied by the device straight into a page-locked host
+    buffer of the caller (a pool per resolution, reused once a result has been polled).
+    Returns (frames/s, latencies in ms, serving stats)."""
+    import torch
+    r.set_precision(precision)
+    pools = _PINNED
+    for key in {(q.W, q.H) for q in reqs}:    # page-locked buffers exist before the clock starts
+        free = pools.setdefault(key, [])
+        need = min(window, sum(1 for q in reqs if (q.W, q.H) == key))
+        while len(free) < need:
+            free.append(torch.empty((key[1], key[0], 3), dtype=torch.float32, pin_memory=True))
+    lat, pending = [], []
+
+    def buf(w_, h_):
+        free = pools[(w_, h_)]
+        return free.pop() if free else torch.empty((h_, w_, 3), dtype=torch.float32, pin_memory=True)
+
+    r.serve_start(max_batch=max_batch, slots=slots)
+    try:
+        t0 = time.perf_counter()
+        i, n = 0, len(reqs)
+        while i < n or pending:
+            now = time.perf_counter() - t0
+            while i < n and (reqs[i].arrival_s <= now if realtime else len(pending) < window):
+                q = reqs[i]
+                b = buf(q.W, q.H)
+                pending.append((r.submit_into(q.view, synth.intrinsics_for(q.W, q.H), q.W, q.H, q.n_levels, q.fs, b),
+                                b, (q.W, q.H)))
+                i += 1
+            still = []
+            for tk, b, key in pending:
+                res, l = r.poll(tk)
+                if l is None:
+                    still.append((tk, b, key))
+                else:
+                    lat.append(1e3 * l)
+                    pools[key].append(b)
+            pending = still
+        span = time.perf_counter() - t0
+        st = r.serve_stats()
+    finally:
+        r.serve_stop()
+    return n / span, lat, st
+
+
+def run_100M(args, lnr, synth, torch, dev, B):
+    """The 100M-point scene resident: batched BF16 at 8 x 1080p per launch (frames/s and
+    visible points/s) and the mixed-resolution serving workload (a seeded Poisson stream of
+    1280x720 / 1920x1080 / 2560x1440 requests, n_levels 4..6, filter_strength U[0.5, 1.5]):
+    served BF16 against the plain per-request FP32 path, then the BF16 arrival rate stepped
+    up to saturation."""
+    from synth.requests import request_stream
+    from synth.workloads import MULTIROOM_100M, make_scene
+    t0 = time.perf_counter()
+    scene = make_scene(MULTIROOM_100M, device=dev)
+    gen_s = time.perf_counter() - t0
+    weights = synth.unet_weights(CH, seed=1)
+    views = synth.random_poses(scene, N_POSES, seed=2)
+    intr = synth.intrinsics_for(W, H)
+    stream = torch.cuda.Stream(device=dev)
+    r = lnr.Renderer(dev.index, stream=stream.cuda_stream)
+    res = {}
+    try:
+        r.load_cloud(scene.xyz, scene.rgb, scene.scan_id)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r.build_grid(CELL)
+        grid_ms = 1e3 * (time.perf_counter() - t0)
+        n_points = int(len(scene.xyz))
+        r.set_unet(CH, weights, "bf16")
+        for (w_, h_) in ((1280, 720), (1920, 1080), (2560, 1440)):
+            r.autotune(w_, h_, B)
+        vis = [r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1] for v in views]
+        out = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
+        fs = [FS[k % 2] for k in range(B)]
+        pick = lambda i: [views[(i * B + k) % len(views)] for k in range(B)]
+        for i in range(3):
+            r.render_batch(pick(i), intr, W, H, NLEV, fs, out=out)
+        torch.cuda.synchronize()
+        K = max(5, args.steps)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        nvis = 0
+        for i in range(K):
+            evs[i][0].record(stream)                 # on the library's stream
+            r.render_batch(pick(3 + i), intr, W, H, NLEV, fs, out=out)
+            evs[i][1].record(stream)
+            nvis += sum(vis[(v_i) % len(views)] for v_i in [((3 + i) * B + k) % len(views) for k in range(B)])
+        torch.cuda.synchronize()
+        ms = float(np.sum([a.elapsed_time(b) for a, b in evs]))
+        res["batched_100M"] = {"value": B * K / (ms * 1e-3), "unit": "frames/s", "steps": K, "views_per_step": B,
+                               "ms_per_step": ms / K, "visible_points_per_s": nvis / (ms * 1e-3),
+                               "visible_points_per_view": float(np.mean(vis)), "n_points": n_points,
+                               "W": W, "H": H, "n_levels": NLEV, "precision": "bf16",
+                               "grid_build_ms": grid_ms, "scene_generation_s": gen_s}
+        del out
+        # ---- mixed-resolution serving ------------------------------------------------
+        n_bf16 = 2000
+        warm = request_stream(scene, 96, None, seed=7)
+        serve_stream(r, lnr, synth, warm, "bf16", B, 3, False)          # graphs, pinned buffers
+        bf16_fps, bf16_lat, st = serve_stream(r, lnr, synth, request_stream(scene, n_bf16, None,
+                                                                              seed=3), "bf16", B, 3, False)
+        n_fp32 = max(60, 6 * args.steps)
+        serve_stream(r, lnr, synth, warm[:6], "fp32", 1, 1, False)
+        fp32_fps, _, _ = serve_stream(r, lnr, synth, request_stream(scene, n_fp32, None, seed=3),
+                                      "fp32", 1, 1, False)
+        lam = 0.7 * fp32_fps
+        n_open = max(60, int(4 * lam))
+        open_reqs = request_stream(scene, n_open, lam, seed=3)
+        _, b_lat, _ = serve_stream(r, lnr, synth, open_reqs, "bf16", B, 3, True)
+        _, f_lat, _ = serve_stream(r, lnr, synth, open_reqs, "fp32", 1, 1, True)
+        sweep = []
+        for mult in (0.25, 0.5, 0.75, 0.9, 1.0, 1.25):
+            lam_k = mult * bf16_fps
+            n_k = 600
+            fps_k, lat_k, st_k = serve_stream(r, lnr, synth, request_stream(scene, n_k, lam_k,
+                                                                            seed=30 + int(100 * mult)),
+                                              "bf16", B, 3, True)
+            sweep.append({"arrivals_per_s": lam_k, "of_closed_loop": mult, "requests": n_k,
+                          "frames_per_s": fps_k, **percentiles(lat_k), "max_batch_seen": st_k["max_batch"],
+                          "peak_slots_busy": st_k.get("peak_busy_slots")})
+        res["served_mix"] = {
+            "workload": "multiroom_100M resident; requests uniform over 1280x720 / 1920x1080 / 2560x1440, "
+                        "n_levels uniform in 4..6, filter_strength U[0.5, 1.5], seeded poses",
+            "served_bf16": {"value": bf16_fps, "unit": "frames/s", "requests": n_bf16, "closed_loop": True,
+                            "max_batch": B, "slots": 3, **percentiles(bf16_lat),
+                            "peak_slots_busy": st.get("peak_busy_slots")},
+            "plain_fp32": {"value": fp32_fps, "unit": "frames/s", "requests": n_fp32, "closed_loop": True},
+            "poisson": {"arrivals_per_s": lam, "requests": n_open, "rule": "0.7 x plain FP32 closed-loop rate",
+                        "served_bf16": percentiles(b_lat), "plain_fp32": percentiles(f_lat)},
+            "bf16_rate_sweep": sweep}
+    finally:
+        r.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,6 +545,7 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-100m", action="store_true", help="skip the 100M-point batched and serving legs")
     ap.add_argument("--accuracy", type=int, default=0, metavar="VIEWS",
                     help="report max abs error and PSNR of the FP32 / BF16 / FP8 U-Nets against the "
                          "oracle's FP64 U-Net on VIEWS 1080p views (slow: the oracle runs on the host)")
@@ -353,8 +558,14 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched path only (no stage timing, plain, serving or CPU legs), "
                          "e.g. under a profiler")
+    ap.add_argument("--replica-selftest", action="store_true",
+                    help="check the multi-rank plumbing on CPU ranks (gloo); no GPU work")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_replicas(args.gpus))
+    if args.replica_selftest:
+        return run_replica_selftest(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -398,13 +609,15 @@ def main():
     r.autotune(W, H, B)          # per-layer conv kernel choice (outside every timed region)
     tune_s = time.perf_counter() - t0
     # every rank renders its own poses (replicas: views are independent)
-    pose = lambda i: views[replica_pose(i, rank, len(views))]
+    pose_idx = lambda i: replica_pose(i, rank, len(views))
+    pose = lambda i: views[pose_idx(i)]
     out = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
+    nlev_run = [NLEV]
 
     def step(i):
         vs = [pose(i * B + k) for k in range(B)]
         fs = [FS[(i * B + k) % 2] for k in range(B)]
-        r.render_batch(vs, intr, W, H, NLEV, fs, out=out)
+        r.render_batch(vs, intr, W, H, nlev_run[0], fs, out=out)
 
     def timed(fn, K, Wm):
         for i in range(Wm):
@@ -444,19 +657,32 @@ def main():
         r.close()
         return
 
-    # ---- stage timing of the batched path (dominant kernel) ------------------------
-    r.set_timing(True)
-    tims = []
-    for i in range(3):
-        step(i)
-        torch.cuda.synchronize()
-        tims.append(r.get_timing())
-    r.set_timing(False)
-    unet_ms = float(np.median([t["unet"] for t in tims]))
+    # ---- stage timing of the batched path (library stage events on its stream) -------
+    vis = [r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1] for v in views]
+
+    def stage_times(nlev, n=3):
+        nlev_run[0] = nlev
+        r.set_timing(True)
+        tims, nv = [], []
+        for i in range(n):
+            step(i)
+            torch.cuda.synchronize()
+            tims.append(r.get_timing())
+            nv.append(sum(vis[pose_idx(i * B + k)] for k in range(B)))
+        r.set_timing(False)
+        nlev_run[0] = NLEV
+        med = {k: float(np.median([t[k] for t in tims]))
+               for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]}
+        return med, float(np.mean(nv))
+
+    stages, nvis_step = stage_times(NLEV)
+    stages0, _ = stage_times(0)
     pk = peaks()
+    hbm = pk.get("hbm_gbs", 6784.5)
+    unet_ms = stages["unet"]
     flops = unet_flops_per_px(CH) * W * H * B
     if have_tc:
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        peak = pk.get("bf16_tflops_sustained", 1713.8)
         roof = {"kernel": "conv3x3 tcgen05 (all U-Net conv launches of a step)", "bound": "tensor",
                 "achieved": flops / (unet_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "measured (bf16_tflops_sustained)"}
@@ -469,6 +695,12 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = conv_traffic() if have_tc else None
     roof["traffic_scope"] = "DRAM bytes read + written by all U-Net conv launches of one step (ncu)"
+    roof_stages = stage_roofline(stages, nvis_step, W * H * B, hbm)
+    filter_cost = {"n_levels": [0, NLEV],
+                   "filter_ms_per_step": [stages0["upsample_pack"], stages["upsample_pack"]],
+                   "resolve_pyramid_ms_per_step": [stages0["resolve_pyramid"], stages["resolve_pyramid"]],
+                   "frame_ms_per_step": [stages0["frame"], stages["frame"]],
+                   "frames_per_s": [B / (stages0["frame"] * 1e-3), B / (stages["frame"] * 1e-3)]}
 
     # ---- plain per-frame FP32 path (device-timed) ----------------------------------
     r.set_precision("fp32")
@@ -484,97 +716,85 @@ def main():
     fp8 = None
     if have_tc:
         try:
-            r.calibrate(views[0], intr, W, H, NLEV, FS[0])
+            r.calibrate(synth.random_poses(scene, 4, seed=77), intr, W, H, NLEV, 1.0)
             r.set_precision("fp8")
             r.autotune(W, H, B)
             fp8_ms, _ = timed(step, args.steps, args.warmup)
             fp8 = {"value": B * args.steps / (float(np.sum(fp8_ms)) / 1e3), "unit": "frames/s",
-                   "calibration": "static per-tensor scales from one BF16 frame (pose 0)"}
+                   "calibration": "static per-tensor scales from 4 BF16 frames of other poses",
+                   "bf16_layers": "encoder level 0 (enc0a, enc0b) and decoder levels 0-1 (dec1a, dec1b, "
+                                  "dec0a, dec0b)"}
         except lnr.LnrError as e:
             fp8 = {"unavailable": str(e)}
         r.set_precision(prec)
 
     # ---- served paths through the public serving API (host result buffers) --------
+    from synth.requests import Request
+
+    def req_list(n, lam, seed, first):
+        arr = np.zeros(n) if lam is None else np.cumsum(np.random.default_rng(seed).exponential(1.0 / lam, size=n))
+        return [Request(float(arr[k]), pose(first + k), W, H, NLEV, FS[k % 2]) for k in range(n)]
+
     def serve_run(precision, max_batch, slots, n, lam, seed):
-        """Submit n 1080p requests (all at once when lam is None, else Poisson arrivals at
-        rate lam); poll every result into a host buffer; return frames/s and latencies."""
-        r.set_precision(precision)
-        r.serve_start(max_batch=max_batch, slots=slots)
-        rng = np.random.default_rng(seed)
-        img = np.empty((H, W, 3), np.float32)
-        lat, pending = [], []
-        try:
-            # warm the configuration (graph capture, pinned buffers)
-            for k in range(2 * max_batch * slots):
-                pending.append(r.submit(pose(k), intr, W, H, NLEV, FS[k % 2]))
-            for tk in pending:
-                while r.poll(tk, img)[0] is None:
-                    pass
-            pending = []
-            arrivals = np.zeros(n) if lam is None else np.cumsum(rng.exponential(1.0 / lam, size=n))
-            t0 = time.perf_counter()
-            i = 0
-            while i < n or pending:
-                now = time.perf_counter() - t0
-                while i < n and arrivals[i] <= now:
-                    pending.append(r.submit(pose(1000 + i), intr, W, H, NLEV, FS[i % 2]))
-                    i += 1
-                still = []
-                for tk in pending:
-                    res, l = r.poll(tk, img)
-                    if res is None:
-                        still.append(tk)
-                    else:
-                        lat.append(l)
-                pending = still
-            span = time.perf_counter() - t0
-        finally:
-            r.serve_stop()
-        return n / span, 1e3 * np.asarray(lat)
+        """n 1080p requests (all at once when lam is None, else Poisson arrivals at rate
+        lam) after a warm-up of the configuration; frames/s and latencies (ms)."""
+        serve_stream(r, lnr, synth, req_list(2 * max_batch * slots, None, seed, 0), precision, max_batch, slots,
+                     False)
+        fps, lat, st = serve_stream(r, lnr, synth, req_list(n, lam, seed, 1000), precision, max_batch, slots,
+                                    lam is not None)
+        return fps, np.asarray(lat), st
 
     lam = 0.7 * plain_fps                      # both paths stable at this arrival rate
     n_open = max(40, int(3 * lam))             # about 3 s of arrivals
     prec_fast = "bf16" if have_tc else "fp32"
-    # closed loop: 320 requests queued at once (about 0.2 s of work), median of three runs
-    # (one short run swings with the host's scheduling of the result copies)
-    srv_runs = [serve_run(prec_fast, 8, 3, 8 * max(40, args.steps), None, 11 + k)[0] for k in range(3)]
+    # closed loop: 320 requests, 48 outstanding at a time (about 0.2 s of work), median of
+    # three runs
+    srv = [serve_run(prec_fast, 8, 3, 8 * max(40, args.steps), None, 11 + k) for k in range(3)]
+    srv_runs = [x[0] for x in srv]
     srv_fps = float(np.median(srv_runs))
-    _, srv_lat = serve_run(prec_fast, 8, 3, n_open, lam, 12)
-    plain_srv_fps, _ = serve_run("fp32", 1, 1, max(10, args.steps), None, 13)
-    _, plain_lat = serve_run("fp32", 1, 1, n_open, lam, 12)
+    _, srv_lat, _ = serve_run(prec_fast, 8, 3, n_open, lam, 12)
+    plain_srv_fps, _, _ = serve_run("fp32", 1, 1, max(10, args.steps), None, 13)
+    _, plain_lat, _ = serve_run("fp32", 1, 1, n_open, lam, 12)
     clk = clocks.stop()
     r.set_precision(prec)
-    e2e = {"value": srv_fps, "unit": "frames/s", "path": "serving API (lnr_submit/lnr_poll), BF16, closed loop",
+    e2e = {"value": srv_fps, "unit": "frames/s",
+           "path": "serving API (lnr_submit_into / lnr_poll), BF16, closed loop with 48 requests outstanding, "
+                   "results copied by the device into page-locked host buffers of the caller",
            "h2d_bytes_per_step": 96 + 24 + 4, "d2h_bytes_per_step": W * H * 3 * 4, "step": "one request",
-           "runs": [round(float(x), 1) for x in srv_runs], "requests_per_run": 8 * max(40, args.steps)}
+           "runs": [round(float(x), 1) for x in srv_runs], "requests_per_run": 8 * max(40, args.steps),
+           "peak_slots_busy": max(x[2].get("peak_busy_slots") or 0 for x in srv)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample(oracle_grid(scene), views, weights)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    r.close()
+    del scene
+
+    big = {}
+    if have_tc and not args.no_100m and world == 1:
+        big = run_100M(args, lnr, synth, torch, dev, B)
 
     launches_per_step = 3 + 1 + 1 + NLEV + 2 * (2 * len(CH) - 1) + (0 if have_tc else 1)  # cull, splat, resolve, upsample, convs
     if rank == 0:
+        cfg = dict(CONFIG)
+        cfg.update({"views_per_step": B, "precision": prec, "parallelism": f"replicas{world}",
+                    "l2": "inputs larger than L2: per-step working set > 1 GB, every step new poses"})
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if have_tc else "f32", "data": "synthetic",
-            "config": {"workload": "multiroom_20M", "W": W, "H": H, "n_points": N_POINTS, "views_per_step": B,
-                       "n_levels": NLEV, "filter_strength": list(FS), "cell": CELL, "unet": list(CH),
-                       "precision": prec, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2: per-step working set > 1 GB, every step new poses"},
-            "latency_ms": {"batched_step": {"p50": float(np.percentile(step_ms, 50)),
-                                            "p99": float(np.percentile(step_ms, 99))},
-                           "served_bf16": {"p50": float(np.percentile(srv_lat, 50)),
-                                           "p99": float(np.percentile(srv_lat, 99)),
-                                           "arrivals_per_s": lam, "requests": int(n_open)},
-                           "plain_fp32": {"p50": float(np.percentile(plain_lat, 50)),
-                                          "p99": float(np.percentile(plain_lat, 99)),
-                                          "arrivals_per_s": lam, "requests": int(n_open)}},
+            "config": cfg,
+            "latency_ms": {"batched_step": percentiles(step_ms),
+                           "served_bf16": {**percentiles(srv_lat), "arrivals_per_s": lam, "requests": int(n_open)},
+                           "plain_fp32": {**percentiles(plain_lat), "arrivals_per_s": lam, "requests": int(n_open)}},
             "plain_fp32": {"value": plain_fps, "unit": "frames/s", "served_value": plain_srv_fps},
             "served_bf16": {"value": srv_fps, "unit": "frames/s"},
             "batched_fp8": fp8,
-            "stages_ms_per_batch": {k: round(float(np.median([t[k] for t in tims])), 4)
-                                    for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]},
+            "stages_ms_per_batch": {k: round(v, 4) for k, v in stages.items()},
+            "visible_points_per_step": nvis_step,
+            "roofline_stages": roof_stages,
+            "filter_cost": filter_cost,
             "grid_build_ms": grid_ms,
             "autotune_s": tune_s,
             "roofline": roof,
@@ -583,9 +803,9 @@ def main():
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
             "wall_s_timed": wall,
+            **big,
         }
         print(json.dumps(line), flush=True)
-    r.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -190,21 +190,32 @@ lnr_status lnr_render_stage(lnr_ctx* ctx, const lnr_view* view, const lnr_intrin
 
 /* Render nviews views of one resolution in one pass: every view's splat, filter and
  * U-Net run batched (the U-Net on an NHWC batch).  views, intr and fs are arrays of
- * nviews; out_rgb holds nviews*H*W*3 floats, view-major.  Same errors as lnr_render. */
+ * nviews; out_rgb holds nviews*H*W*3 floats, view-major.  With out_on_device the U-Net
+ * writes out_rgb directly (the frame's CUDA graph is kept per output buffer, for up to 32
+ * buffers).  One resolution and pyramid depth per call: views of other sizes go to other
+ * calls, or to the serving loop, which runs batches of different sizes side by side on
+ * its slots.  Same errors as lnr_render. */
 lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
                             const lnr_intrinsics* intr, int W, int H, int n_levels,
                             const float* fs, float* out_rgb, int out_on_device);
 
 /* Calibrate the FP8 (E4M3) U-Net on one view (after set_unet): the view is rendered with
  * the BF16 U-Net, the largest magnitude of every convolution's output sets that tensor's
- * static scale (8 x amax / 448: headroom for views with larger activations), and E4M3
- * weights with per-output-channel scales are built with the input scales folded in;
- * accumulation stays FP32 (the paper states no precision; reduced precision is this
- * library's addition).  Afterwards lnr_set_precision(LNR_FP8) is allowed.  Arguments
- * as lnr_render.  Errors: as lnr_render; LNR_E_ARG when a channel count of the net is not a
- * multiple of 32. */
+ * static scale (headroom x amax / 448; the headroom leaves room for views with larger
+ * activations), and E4M3 weights with per-output-channel scales are built with the input
+ * scales folded in; accumulation stays FP32 (the paper states no precision; reduced
+ * precision is this library's addition).  Afterwards lnr_set_precision(LNR_FP8) is
+ * allowed.  Arguments as lnr_render.  Errors: as lnr_render; LNR_E_ARG when a channel count
+ * of the net is not a multiple of 32. */
 lnr_status lnr_calibrate(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
                          int H, int n_levels, float fs);
+
+/* The same calibration over nviews views rendered as one batch (arrays as
+ * lnr_render_batch): every tensor's scale comes from its largest magnitude over all of
+ * them, so the scales cover the spread of activations between views. */
+lnr_status lnr_calibrate_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
+                               const lnr_intrinsics* intr, int W, int H, int n_levels,
+                               const float* fs);
 
 /* Autotune the tensor-core U-Net for batches of `batch` views at W x H (part of this
  * library's batching; the paper has no counterpart): for every convolution, every valid
@@ -220,11 +231,14 @@ lnr_status lnr_autotune(lnr_ctx* ctx, int W, int H, int batch);
 /* ---- serving: continuous batching of render requests ------------------------------ */
 
 /* Start the serving loop: up to max_batch requests of one resolution per launch, up to
- * `slots` launches in flight on separate streams, admission bounded by the activation
- * bytes of the requests in flight (lnr_set_memory_budget; 0 = no bound).  Uses the
- * precision selected by set_unet / set_precision. */
+ * `slots` launches in flight on separate streams.  Uses the precision selected by
+ * set_unet / set_precision at this call. */
 lnr_status lnr_serve_start(lnr_ctx* ctx, int max_batch, int slots);
 lnr_status lnr_serve_stop(lnr_ctx* ctx);
+/* Device-memory budget of the serving loop's slots (0 = no bound): a batch is admitted when
+ * the buffers of the slots already busy plus the batch's own need fit, and slots release
+ * buffers they no longer need so that all slots together hold at most `bytes` (a single
+ * request larger than the budget still runs, alone). */
 lnr_status lnr_set_memory_budget(lnr_ctx* ctx, size_t bytes);
 
 /* Queue one render request; *ticket identifies it.  Thread-safe.  Arguments as
@@ -232,14 +246,25 @@ lnr_status lnr_set_memory_budget(lnr_ctx* ctx, size_t bytes);
 lnr_status lnr_submit(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
                       int H, int n_levels, float fs, uint64_t* ticket);
 
+/* As lnr_submit, with the result's destination given now: out_rgb (host, H*W*3 floats,
+ * owned by the caller, valid and untouched until lnr_poll reports the request done).  When
+ * out_rgb is page-locked (cudaHostAlloc / cudaHostRegister) the device copies the result
+ * straight into it and lnr_poll copies nothing; otherwise the result goes through the
+ * library's page-locked buffers and lnr_poll copies it into out_rgb (when its own out_rgb
+ * is null).  Thread-safe.  Part of this library's serving; the paper has no counterpart. */
+lnr_status lnr_submit_into(lnr_ctx* ctx, const lnr_view* view, const lnr_intrinsics* intr, int W,
+                           int H, int n_levels, float fs, float* out_rgb, uint64_t* ticket);
+
 /* Result of a request: LNR_E_BUSY until it is done, then copies H*W*3 floats to out_rgb
  * (host, nullable) and its latency (completion minus submission, seconds) to
  * *latency_s (nullable), and forgets the request.  Thread-safe. */
 lnr_status lnr_poll(lnr_ctx* ctx, uint64_t ticket, float* out_rgb, double* latency_s);
 
 /* Serving counters: out[0] requests done, out[1] launches, out[2] largest batch,
- * out[3] peak activation bytes in flight.  Thread-safe. */
-lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[4]);
+ * out[3] peak device bytes admitted (busy slots' buffers plus the batch being admitted),
+ * out[4] peak device bytes held by all slots' buffers, out[5] peak number of slots with work
+ * on the device at once.  out holds 6 values.  Thread-safe. */
+lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[6]);
 
 /* ---- measurement ------------------------------------------------------------------- */
 

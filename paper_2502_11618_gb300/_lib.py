@@ -24,8 +24,8 @@ E_BUSY = -6
 SYMBOLS = ["lnr_create", "lnr_destroy", "lnr_last_error", "lnr_load_cloud", "lnr_build_grid",
            "lnr_grid_info", "lnr_set_unet", "lnr_set_precision", "lnr_render", "lnr_render_stage",
            "lnr_render_batch", "lnr_serve_start", "lnr_serve_stop", "lnr_set_memory_budget",
-           "lnr_submit", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
-           "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_set_soft_zbuffer",
+           "lnr_submit", "lnr_submit_into", "lnr_poll", "lnr_serve_stats", "lnr_set_timing", "lnr_get_timing",
+           "lnr_filter_static", "lnr_autotune", "lnr_calibrate", "lnr_calibrate_batch", "lnr_set_soft_zbuffer",
            "lnr_training_input", "lnr_build_grid_frame", "lnr_set_shard", "lnr_shard_resolve",
            "lnr_shard_finish", "lnr_probe_atomic_rate"]
 
@@ -85,6 +85,7 @@ def lib():
             "lnr_serve_stop": ([p], st),
             "lnr_set_memory_budget": ([p, sz], st),
             "lnr_submit": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, C.POINTER(u64)], st),
+            "lnr_submit_into": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f, p, C.POINTER(u64)], st),
             "lnr_poll": ([p, u64, p, C.POINTER(d)], st),
             "lnr_serve_stats": ([p, p], st),
             "lnr_set_timing": ([p, i], st),
@@ -93,6 +94,7 @@ def lib():
             "lnr_filter_static": ([p, i, i, i, f, p, p], st),
             "lnr_autotune": ([p, i, i, i], st),
             "lnr_calibrate": ([p, C.POINTER(View), C.POINTER(Intrinsics), i, i, i, f], st),
+            "lnr_calibrate_batch": ([p, i, p, p, i, i, i, p], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -210,7 +212,17 @@ class Renderer:
         self.levels = len(ch)
 
     def calibrate(self, view, intr, W, H, n_levels, fs):
-        """Static E4M3 scales from one BF16 frame; enables the FP8 precision."""
+        """Static E4M3 scales from BF16 frames; enables the FP8 precision.  `view` may be a
+        list of views (calibrated as one batch; fs a scalar or one per view)."""
+        if isinstance(view, (list, tuple)):
+            n = len(view)
+            va = (View * n)(*[make_view(v) for v in view])
+            intrs = intr if isinstance(intr, (list, tuple)) else [intr] * n
+            ia = (Intrinsics * n)(*[make_intr(k) for k in intrs])
+            fsa = np.ascontiguousarray(np.broadcast_to(np.asarray(fs, np.float32), (n,)))
+            self._check(self._L.lnr_calibrate_batch(self._c, n, C.cast(va, C.c_void_p), C.cast(ia, C.c_void_p),
+                                                    W, H, n_levels, _ptr(fsa)))
+            return
         self._check(self._L.lnr_calibrate(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)), W, H,
                                           n_levels, float(fs)))
 
@@ -314,6 +326,16 @@ class Renderer:
                                        n_levels, float(fs), C.byref(t)))
         return t.value
 
+    def submit_into(self, view, intr, W, H, n_levels, fs, out) -> int:
+        """Queue a request whose result goes to `out` (host, (H, W, 3) float32, kept alive
+        by the caller until poll reports it done).  A page-locked `out` (e.g. a torch
+        tensor from pin_memory()) receives the result straight from the device."""
+        t = C.c_uint64()
+        ptr = C.c_void_p(out.data_ptr()) if hasattr(out, "data_ptr") else _ptr(out)
+        self._check(self._L.lnr_submit_into(self._c, C.byref(make_view(view)), C.byref(make_intr(intr)), W, H,
+                                            n_levels, float(fs), ptr, C.byref(t)))
+        return t.value
+
     def poll(self, ticket, out=None):
         """(image or None, latency_s); image None while the request is in flight."""
         lat = C.c_double()
@@ -324,9 +346,10 @@ class Renderer:
         return out, lat.value
 
     def serve_stats(self):
-        o = np.zeros(4, np.uint64)
+        o = np.zeros(6, np.uint64)
         self._check(self._L.lnr_serve_stats(self._c, _ptr(o)))
-        return dict(done=int(o[0]), launches=int(o[1]), max_batch=int(o[2]), peak_act_bytes=int(o[3]))
+        return dict(done=int(o[0]), launches=int(o[1]), max_batch=int(o[2]), peak_act_bytes=int(o[3]),
+                    peak_alloc_bytes=int(o[4]), peak_busy_slots=int(o[5]))
 
     # --- measurement --------------------------------------------------------------------
     def set_timing(self, enable=True):

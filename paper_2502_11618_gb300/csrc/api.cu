@@ -27,18 +27,31 @@ lnr_status cuda_fail(lnr_ctx* c, cudaError_t e, const char* where) {
 }
 
 void Workspace::release() {
-    DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_cell, &vis_pref, &vis_tot, &chunk_cell, &keys,
+    DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_info, &vis_pref, &vis_tot, &chunk_cell, &keys,
                    &soft_acc, &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
     for (DBuf* b : all) b->release();
     for (auto& a : act) a.release();
-    if (pinned_view.p) cudaFreeHost(pinned_view.p);
-    pinned_view.p = nullptr;
-    pinned_view.bytes = 0;
+    for (auto& pv : pinned_view) {
+        if (pv.p) cudaFreeHost(pv.p);
+        pv.p = nullptr;
+        pv.bytes = 0;
+    }
     for (auto& e : ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto& e : view_ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
     graph_warm.clear();
+}
+
+size_t Workspace::device_bytes() const {
+    const DBuf* all[] = {&view, &cull_flag, &cull_cnt, &cull_bsum, &vis_info, &vis_pref, &vis_tot, &chunk_cell,
+                         &keys, &soft_acc, &depth, &rgba, &pyr_m, &pyr_u, &u0, &out};
+    size_t n = 0;
+    for (const DBuf* b : all) n += b->bytes;
+    for (const auto& a : act) n += a.bytes;
+    return n;
 }
 
 // FP64 composition of the view with the grid (once per view, on the host): the anchor
@@ -101,7 +114,7 @@ lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const
 // Size every per-frame buffer for B views of W x H with nlev pyramid levels.
 static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int H, int nlev) {
     cudaError_t e;
-    const void* before[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
+    const void* before[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_info.p, ws.vis_pref.p,
                             ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
                             ws.soft_acc.p, ws.chunk_cell.p};
     const size_t P = (size_t)W * H;
@@ -109,7 +122,7 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
     const size_t pf = pyramid_floats(W, H, kMaxLevels);
     if ((e = ws.view.ensure(sizeof(ViewDev) * B)) || (e = ws.cull_flag.ensure(4 * c->ncells * B)) ||
         (e = ws.cull_cnt.ensure(4 * c->ncells * B)) || (e = ws.cull_bsum.ensure(8 * (size_t)nb * B)) ||
-        (e = ws.vis_cell.ensure(4 * c->ncells * B)) || (e = ws.vis_pref.ensure(4 * c->ncells * B)) ||
+        (e = ws.vis_info.ensure(16 * c->ncells * B)) || (e = ws.vis_pref.ensure(4 * c->ncells * B)) ||
         (e = ws.vis_tot.ensure(8 * B)) || (e = ws.chunk_cell.ensure(4 * splat_max_chunks(c->n) * B)) ||
         (e = ws.depth.ensure(4 * P * B)) || (e = ws.rgba.ensure(4 * P * B)) ||
         (e = ws.pyr_m.ensure(4 * pf * B)) || (e = ws.pyr_u.ensure(4 * pf * B)) || (e = ws.u0.ensure(4 * P * B)) ||
@@ -123,15 +136,22 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
         if ((e = ws.soft_acc.ensure(16 * P * B))) return e;
         if (new_acc) ws.soft_dirty = true;
     }
-    if (ws.pinned_view.bytes < sizeof(ViewDev) * B) {
-        if (ws.pinned_view.p) cudaFreeHost(ws.pinned_view.p);
-        if ((e = cudaMallocHost(&ws.pinned_view.p, sizeof(ViewDev) * B))) return e;
-        ws.pinned_view.bytes = sizeof(ViewDev) * B;
-    }
+    for (auto& pv : ws.pinned_view)
+        if (pv.bytes < sizeof(ViewDev) * B) {
+            if (pv.p) cudaFreeHost(pv.p);
+            pv.p = nullptr;
+            pv.bytes = 0;
+            if ((e = cudaMallocHost(&pv.p, sizeof(ViewDev) * B))) return e;
+            pv.bytes = sizeof(ViewDev) * B;
+            ws.alloc_gen++;  // captured graphs upload from the old block
+        }
     if (!ws.ev[0])
         for (auto& ev : ws.ev)
             if ((e = cudaEventCreate(&ev))) return e;
-    const void* after[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_cell.p, ws.vis_pref.p,
+    if (!ws.view_ev[0])
+        for (auto& ev : ws.view_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return e;
+    const void* after[] = {ws.view.p, ws.cull_flag.p, ws.cull_cnt.p, ws.cull_bsum.p, ws.vis_info.p, ws.vis_pref.p,
                            ws.vis_tot.p, ws.depth.p, ws.rgba.p, ws.pyr_m.p, ws.pyr_u.p, ws.u0.p, ws.out.p, ws.keys.p,
                            ws.soft_acc.p, ws.chunk_cell.p};
     for (size_t i = 0; i < sizeof(before) / sizeof(before[0]); ++i)
@@ -143,6 +163,16 @@ static cudaError_t ensure_ws(const lnr_ctx* c, Workspace& ws, int B, int W, int 
     return cudaSuccess;
 }
 
+// The upload of the frame's view block is done once view_ev[vk] completes.  Under stream
+// capture the record becomes a node of its own (an external event record), so that every
+// replay of the graph records it; outside capture it is a plain record.
+static void record_view_uploaded(Workspace& ws, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ws.view_ev[ws.vk], st, cudaEventRecordExternal);
+    else cudaEventRecord(ws.view_ev[ws.vk], st);
+}
+
 // Enqueue one batch on `st`: params upload, cull, splat, resolve + pyramid, upsampling,
 // U-Net.  stage < 0 runs the whole frame into ws.out; otherwise stops after that stage.
 void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec,
@@ -152,7 +182,8 @@ void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_pr
         if (timed) cudaEventRecord(ev[i], st);
     };
     mark(0);
-    cudaMemcpyAsync(ws.view.p, ws.pinned_view.p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws.view.p, ws.pinned_view[ws.vk].p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    record_view_uploaded(ws, st);
     if (ws.keys_dirty) launch_clear_keys(ws, st);
     launch_cull(c, ws, st);
     mark(1);
@@ -173,14 +204,15 @@ void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_pr
     launch_upsample(c, ws, 0, unet_in, kind, stage == LNR_STAGE_FILTERED, st);
     mark(4);
     if (stage >= 0) return;
-    unet_forward(c, ws, prec, unet_in, ws.out.as<float>(), st, nullptr);
+    unet_forward(c, ws, prec, unet_in, ws.out_ptr ? ws.out_ptr : ws.out.as<float>(), st, nullptr);
     mark(5);
 }
 
 void enqueue_from_keys(lnr_ctx* c, Workspace& ws, cudaStream_t st, const uint64_t* keys, const uint32_t* rgba,
                        int stage, lnr_precision prec) {
     const size_t P = (size_t)ws.W * ws.H;
-    cudaMemcpyAsync(ws.view.p, ws.pinned_view.p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws.view.p, ws.pinned_view[ws.vk].p, sizeof(ViewDev) * ws.B, cudaMemcpyHostToDevice, st);
+    record_view_uploaded(ws, st);
     cudaMemcpyAsync(ws.keys.p, keys, 8 * P, cudaMemcpyDeviceToDevice, st);
     launch_resolve_pyramid(c, ws, st);  // depth, pyramid, this context's colours; clears the keys
     if (rgba) cudaMemcpyAsync(ws.rgba.p, rgba, 4 * P, cudaMemcpyDeviceToDevice, st);
@@ -194,31 +226,35 @@ void enqueue_from_keys(lnr_ctx* c, Workspace& ws, cudaStream_t st, const uint64_
 }
 
 lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in,
-                                int W, int H, int nlev, const float* fs) {
+                                int W, int H, int nlev, const float* fs, lnr_precision prec) {
     cudaError_t e = ensure_ws(c, ws, B, W, H, nlev);
     if (e != cudaSuccess) return cuda_fail(c, e, "workspace");
     const void* in_before = ws.act[4 * kMaxUnetLevels].p;
-    e = ws.act[4 * kMaxUnetLevels].ensure((size_t)B * W * H * 8 * 4 + 256);
+    e = ws.act[4 * kMaxUnetLevels].ensure((size_t)B * W * H * unet_in_bytes_per_px(prec) + 256);
     if (e != cudaSuccess) return cuda_fail(c, e, "U-Net input");
     if (in_before != ws.act[4 * kMaxUnetLevels].p) ws.alloc_gen++;
     if (c->unet_ok) {
-        e = unet_ensure(c->unet, ws, c->prec == LNR_FP32 ? LNR_FP32 : LNR_BF16);
-        if (e == cudaSuccess && c->prec != LNR_FP32) e = unet_ensure(c->unet, ws, LNR_FP32);
+        e = unet_ensure(c->unet, ws, prec);
         if (e != cudaSuccess) return cuda_fail(c, e, "U-Net activations");
     }
-    ViewDev* hv = ws.pinned_view.as<ViewDev>();
-    // the pinned block may still feed an earlier launch on this stream
-    e = cudaStreamSynchronize(ws.stream);
+    ws.out_ptr = nullptr;
+    // the block this frame's parameters go into: wait for the upload that used it last
+    ws.vk = (int)(ws.vcount++ & 1);
+    e = cudaEventSynchronize(ws.view_ev[ws.vk]);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    ViewDev* hv = ws.pinned_view[ws.vk].as<ViewDev>();
     for (int i = 0; i < B; ++i) compose_view(c, views[i], in[i], fs[i], hv[i]);
     return LNR_OK;
 }
 
-size_t frame_bytes(int B, int W, int H, bool soft) {
+size_t frame_bytes(const lnr_ctx* c, int B, int W, int H, bool soft) {
     const size_t P = (size_t)B * W * H;
     // keys 8, depth 4, rgba 4, kept depth 4, output 12, U-Net input 32 bytes per pixel, pyramid;
-    // soft z-buffer sums 16
-    return P * (soft ? 80 : 64) + 8 * (size_t)B * pyramid_floats(W, H, kMaxLevels);
+    // soft z-buffer sums 16; per view the cull and compaction tables (28 bytes per cell, block
+    // sums, the splat's chunk table) and the view parameters
+    const size_t per_view = 28 * (size_t)c->ncells + 8 * (size_t)cull_blocks(c->ncells) +
+                            4 * splat_max_chunks(c->n) + sizeof(ViewDev) + 8;
+    return P * (soft ? 80 : 64) + 8 * (size_t)B * pyramid_floats(W, H, kMaxLevels) + (size_t)B * per_view + 16 * 256;
 }
 
 // Enqueue a whole frame batch on ws.stream: replayed from a CUDA graph captured for this
@@ -229,8 +265,10 @@ cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_gr
         enqueue_frame(c, ws, ws.stream, -1, prec, false);
         return cudaGetLastError();
     }
-    const GraphKey key{ws.B, ws.W, ws.H, ws.nlev, (int)prec};
-    if (ws.graph_gen != ws.alloc_gen || ws.graph_cloud != c->cloud_gen || ws.graph_unet != c->unet_gen) {
+    const GraphKey key{ws.B, ws.W, ws.H, ws.nlev, (int)prec, ws.vk, ws.out_ptr};
+    // graphs for many different caller buffers are not kept: start over past 32
+    if (ws.graph_gen != ws.alloc_gen || ws.graph_cloud != c->cloud_gen || ws.graph_unet != c->unet_gen ||
+        ws.graphs.size() >= 32) {
         for (auto& kv : ws.graphs) cudaGraphExecDestroy(kv.second);
         ws.graphs.clear();
         ws.graph_warm.clear();
@@ -275,8 +313,10 @@ static void read_timing(lnr_ctx* c, Workspace& ws) {
 }
 
 static lnr_status finish_output(lnr_ctx* c, Workspace& ws, float* out, size_t nfloat, int on_device) {
-    cudaError_t e = cudaMemcpyAsync(out, ws.out.p, nfloat * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    ws.stream);
+    cudaError_t e = cudaSuccess;
+    if (out != ws.out_ptr)  // else the U-Net wrote the caller's device buffer directly
+        e = cudaMemcpyAsync(out, ws.out.p, nfloat * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            ws.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "output copy");
     if (!on_device || c->timing) {
         e = cudaStreamSynchronize(ws.stream);
@@ -447,7 +487,7 @@ lnr_status lnr_shard_resolve(lnr_ctx* c, const lnr_view* view, const lnr_intrins
     if (c->soft_rel > 0.0f) return fail(c, LNR_E_STATE, "cloud shards use the hard z-buffer");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, 1, view, in, W, H, 0, &fs);
+    s = prepare_views(c, ws, 1, view, in, W, H, 0, &fs, c->prec);
     if (s != LNR_OK) return s;
     enqueue_from_keys(c, ws, ws.stream, keys, nullptr, LNR_STAGE_RGBDA_RAW, c->prec);
     cudaError_t e = cudaMemcpyAsync(rgba, ws.rgba.p, 4 * (size_t)W * H, cudaMemcpyDeviceToDevice, ws.stream);
@@ -467,7 +507,7 @@ lnr_status lnr_shard_finish(lnr_ctx* c, const lnr_view* view, const lnr_intrinsi
     if (!keys || !rgba || !out) return fail(c, LNR_E_ARG, "null keys, colours or output");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs, c->prec);
     if (s != LNR_OK) return s;
     enqueue_from_keys(c, ws, ws.stream, keys, rgba, -1, c->prec);
     const size_t bytes = 12 * (size_t)W * H;
@@ -626,8 +666,9 @@ lnr_status lnr_render_batch(lnr_ctx* c, int nviews, const lnr_view* views, const
     if (!out) return fail(c, LNR_E_ARG, "null output");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, nviews, views, in, W, H, nlev, fs);
+    s = prepare_views(c, ws, nviews, views, in, W, H, nlev, fs, c->prec);
     if (s != LNR_OK) return s;
+    if (on_device) ws.out_ptr = out;  // the U-Net head writes the caller's buffer
     if (c->timing) enqueue_frame(c, ws, ws.stream, -1, c->prec, true);
     else {
         cudaError_t e = run_frame(c, ws, c->prec, true);
@@ -649,7 +690,7 @@ lnr_status lnr_training_input(lnr_ctx* c, const lnr_view* view, const lnr_intrin
     if (!gt_rgb || !out) return fail(c, LNR_E_ARG, "null ground truth or output");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs, c->prec);
     if (s != LNR_OK) return s;
     enqueue_frame(c, ws, ws.stream, LNR_STAGE_FILTERED, c->prec, false);
     const size_t P = (size_t)W * H;
@@ -678,7 +719,7 @@ lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsi
     if (!out) return fail(c, LNR_E_ARG, "null output");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs, c->prec);
     if (s != LNR_OK) return s;
     enqueue_frame(c, ws, ws.stream, stage, c->prec, false);
     const size_t P = (size_t)W * H;
@@ -733,8 +774,13 @@ lnr_status lnr_render_stage(lnr_ctx* c, const lnr_view* view, const lnr_intrinsi
 }
 
 lnr_status lnr_calibrate(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in, int W, int H, int nlev, float fs) {
+    return lnr_calibrate_batch(c, 1, view, in, W, H, nlev, &fs);
+}
+
+lnr_status lnr_calibrate_batch(lnr_ctx* c, int nviews, const lnr_view* view, const lnr_intrinsics* in, int W, int H,
+                               int nlev, const float* fs) {
     if (!c) return LNR_E_ARG;
-    lnr_status s = check_frame_args(c, 1, view, in, W, H, nlev, &fs, true);
+    lnr_status s = check_frame_args(c, nviews, view, in, W, H, nlev, fs, true);
     if (s != LNR_OK) return s;
     if (c->prec == LNR_FP32 && !tc_available()) return fail(c, LNR_E_ARG, "no tensor-core path in this library");
     for (const auto& L : c->unet.convs)
@@ -742,7 +788,7 @@ lnr_status lnr_calibrate(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics*
             return fail(c, LNR_E_ARG, "FP8 needs every U-Net channel count to be a multiple of 32");
     cudaSetDevice(c->device);
     Workspace& ws = c->ws;
-    s = prepare_views(c, ws, 1, view, in, W, H, nlev, &fs);
+    s = prepare_views(c, ws, nviews, view, in, W, H, nlev, fs, LNR_BF16);  // the calibration frames run in BF16
     if (s != LNR_OK) return s;
     enqueue_frame(c, ws, ws.stream, -1, LNR_BF16, false);
     cudaError_t e = cudaStreamSynchronize(ws.stream);
@@ -765,7 +811,7 @@ lnr_status lnr_autotune(lnr_ctx* c, int W, int H, int batch) {
     ws.H = H;
     const void* in_before = ws.act[4 * kMaxUnetLevels].p;
     const void* out_before = ws.out.p;
-    if (!e) e = ws.act[4 * kMaxUnetLevels].ensure((size_t)batch * W * H * 8 * 4 + 256);
+    if (!e) e = ws.act[4 * kMaxUnetLevels].ensure((size_t)batch * W * H * unet_in_bytes_per_px(c->prec) + 256);
     if (!e) e = ws.out.ensure((size_t)batch * W * H * 12);
     if (!e) e = unet_ensure(c->unet, ws, LNR_FP32);
     if (e != cudaSuccess) return cuda_fail(c, e, "autotune buffers");

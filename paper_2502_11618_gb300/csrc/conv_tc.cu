@@ -107,12 +107,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of parity `parity`: false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase of parity `parity`: false after `limit` cycles (~2 s by default).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -437,7 +437,9 @@ struct HSeg {
     int wblk;        // weight blocks per chunk in memory (9, or 16 for the coarse operand)
     int bload;       // blocks staged per chunk (9; coarse: 16 for 4 classes, else the tile's y class's 8)
     int bsel;        // 1: the staged blocks start at 8 * (tile's y class)
-    int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel
+    int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel; or
+                     // 8 (16 bytes, the network input): tap pairs, see issue_paired
+    int paired;      // 1: 8-channel input, K = 16 per MMA covers two horizontal taps
     int rows;        // halo rows staged
     int nchunk;      // K chunks of this segment
     uint32_t pitch;  // bytes per staged pixel (= ck * 2)
@@ -476,6 +478,13 @@ struct HParams {
     // parameter bank) rather than shared memory, whose bandwidth the MMAs' operand reads
     // already use up: bias, accumulator scale (E4M3 operands, else 1), and the fused head's
     // weights [4][N] (zero past head_o) followed by its 4 biases.
+    // Bounded waits: cycles before a wait gives up (kWaitCycles); stall = 1 makes the MMA
+    // issuer first wait on a barrier that nothing arrives on (the timeout test's switch, with
+    // a short wait_cycles so that the whole launch ends within milliseconds).
+    long long wait_cycles;
+    int stall;
+    int tbufs;  // TMEM accumulator buffers: 2 (the epilogue of a tile overlaps the next tile's
+                // MMAs) or 1 (tiles of up to 512 accumulator columns; each weight stage feeds more MMAs)
     alignas(16) float cbias[kHaloMaxN];
     alignas(16) float cscale[kHaloMaxN];
     alignas(16) float chead[4 * kHaloMaxN + 4];
@@ -740,6 +749,51 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
     }
 }
 
+// The first conv, whose input has 8 channels (16 bytes per pixel, staged without swizzle):
+// a K = 16 MMA takes two horizontal taps at once.  Its A operand starts at the pixel of the
+// first tap, and the second half of K (the second 8-column core matrix) is read 16 bytes
+// on -- the next pixel -- by a leading-byte offset of 16.  Pair 0 covers taps kx = 0 and 1;
+// pair 1 starts one pixel on and covers a zero weight block and tap kx = 2.  Weight blocks
+// per pair: [first half: ky = 2, 1, 0][second half: ky = 2, 1, 0], N x 16 bytes each, so the
+// B operand's second half lies 3 blocks on.  Rows are issued as in issue_stage.
+template <int R>
+__device__ __forceinline__ void issue_paired(const IssueCtx& q, uint32_t a0, uint32_t b0, uint32_t d0, bool first) {
+    constexpr int PER = IssueSplit<R, 0>::per;
+    const uint32_t N = q.N;
+    const uint32_t row16 = kHaloW;  // one staged row of 130 pixels, in 16-byte units
+    // no swizzle: LBO (bits 16-29) and SBO (bits 32-45) in 16-byte units, version bit 46
+    const uint64_t hia = ((uint64_t)1 << 16) | ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
+    const uint64_t hib = ((uint64_t)(3 * N) << 16) | ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
+    const uint32_t d = d0 + (uint32_t)(q.g * PER) * N;
+    const uint32_t a = a0 + (uint32_t)(q.g * PER) * row16;
+    const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const uint32_t aj = a + (uint32_t)j, bj = b0 + (uint32_t)(6 * j) * N;
+        if (j == 0) {
+#pragma unroll
+            for (int r = 0; r < PER; ++r)
+                mma_bf16(d + (uint32_t)r * N, hia | (uint64_t)(aj + (uint32_t)r * row16), hib | (uint64_t)(bj + 2 * N),
+                         q.idesc, acc0);
+#pragma unroll
+            for (int h = 1; h < PER + 2; ++h) {
+                const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h - 1 < PER - 1 ? h - 1 : PER - 1;
+                const int blk = 2 - (h - rlo);
+                mma_bf16(d + (uint32_t)rlo * N, hia | (uint64_t)(aj + (uint32_t)h * row16),
+                         hib | (uint64_t)(bj + (uint32_t)blk * N), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < PER + 2; ++h) {
+                const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h < PER - 1 ? h : PER - 1;
+                const int blk = 2 - (h - rlo);
+                mma_bf16(d + (uint32_t)rlo * N, hia | (uint64_t)(aj + (uint32_t)h * row16),
+                         hib | (uint64_t)(bj + (uint32_t)blk * N), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
+            }
+        }
+    }
+}
+
 // PAR = 0: standard tiles of R rows x 128 columns.  PAR = 1, 2 or 4: the decoder's first
 // conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
@@ -760,9 +814,11 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     auto tempty = [&](int b) { return bars + 8u * (2 * S + 2 + b); };
     const uint32_t drain = bars + 8u * (2 * S + 4);
     const uint32_t tslot = bars + 8u * (2 * S + 5);
+    const uint32_t never = bars + 8u * (2 * S + 6);  // no thread ever arrives on it
     volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N;
+    const long long lim = p.wait_cycles;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
@@ -773,6 +829,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
             mbar_init(tempty(b), EPI);
         }
         mbar_init(drain, p.nmma);
+        mbar_init(never, 1);
         *flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -818,7 +875,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
             for (int sg = 0; sg < p.nseg && ok; ++sg) {
                 const HSeg& s = p.seg[sg];
                 for (int cc = 0; cc < s.nchunk; ++cc) {
-                    if (!mbar_wait(empty(st), ph)) { ok = false; break; }
+                    if (!mbar_wait(empty(st), ph, lim)) { ok = false; break; }
                     const uint32_t a_dst = base + st * p.stage_bytes;
                     mbar_expect_tx(full(st), s.bytes);
                     const int c = cc * s.ck;
@@ -840,7 +897,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
             }
         }
         if (!ok) atomicExch(p.err, 5);
-        for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1);
+        for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(full(k % S), (k / S) & 1, lim);
     } else if (warp >= 1 && warp <= MW && lane == 0 && warp - 1 < p.nmma) {
         // ----------------------------------------------------------------- MMA --
         // Issuer g owns work units [a_lo, a_hi] of every tile: standard tiles one output row
@@ -855,14 +912,15 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         int tcount = 0;
         int st = 0;        // stage (use % S, kept incrementally)
         uint32_t ph = 0u;  // parity that the stage's full barrier must reach
-        bool ok = true, issued = false;
+        bool ok = !p.stall || mbar_wait(never, 0, lim), issued = false;
         for (int t = blockIdx.x; tile_live(t) && ok; t += gridDim.x, ++tcount) {
             int n, x0, y0, px, py;
             tile_of(t, n, x0, y0, px, py);
             q.px = px;
             q.py = py;
-            const int b = tcount & 1;
-            if (!mbar_wait(tempty(b), ((tcount >> 1) & 1) ^ 1)) { ok = false; break; }
+            const int b = p.tbufs == 2 ? (tcount & 1) : 0;
+            const int u = p.tbufs == 2 ? (tcount >> 1) : tcount;  // uses of buffer b so far
+            if (!mbar_wait(tempty(b), (u & 1) ^ 1, lim)) { ok = false; break; }
             tc_fence_after();
             constexpr int NACC = R * (PAR == 0 ? 1 : PAR);
             const uint32_t d0 = tmem + (uint32_t)(b * NACC * N);
@@ -870,11 +928,12 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                 const HSeg& s = p.seg[sg];
                 const int nk = (int)(s.pitch >> 5);  // one MMA per 32 bytes of K (16 BF16 or 32 E4M3)
                 for (int cc = 0; cc < s.nchunk; ++cc) {
-                    if (!mbar_wait(full(st), ph)) { ok = false; break; }
+                    if (!mbar_wait(full(st), ph, lim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
                     const uint32_t b0 = a0 + (s.b_off >> 4);
-                    switch (nk) {
+                    if (PAR == 0 && !IN8 && s.paired) issue_paired<R>(q, a0, b0, d0, cc == 0);
+                    else switch (nk) {
                         case 1: issue_stage<R, PAR, IN8, 1>(q, sg, a0, b0, s, d0, cc == 0); break;
                         case 2: issue_stage<R, PAR, IN8, 2>(q, sg, a0, b0, s, d0, cc == 0); break;
                         default: issue_stage<R, PAR, IN8, 4>(q, sg, a0, b0, s, d0, cc == 0); break;
@@ -894,7 +953,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         // issued has completed before TMEM is released
         (void)issued;
         mma_commit(drain);
-        mbar_wait(drain, 0);
+        mbar_wait(drain, 0, lim);
     } else if (warp > MW) {
         // ------------------------------------------------------------ epilogue --
         const int q = warp & 3;
@@ -926,8 +985,9 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
         int tcount = 0;
         int oc = 0;  // rows (row pairs) this warp has staged: selects the staging buffer
         for (int t = blockIdx.x; tile_live(t); t += gridDim.x, ++tcount) {
-            const int b = tcount & 1;
-            if (leader && !mbar_wait(tfull(b), (tcount >> 1) & 1)) *flag = 1;
+            const int b = p.tbufs == 2 ? (tcount & 1) : 0;
+            const int u = p.tbufs == 2 ? (tcount >> 1) : tcount;
+            if (leader && !mbar_wait(tfull(b), u & 1, lim)) *flag = 1;
             named_sync(1, 32 * EPI);
             if (*flag) break;
             tc_fence_after();
@@ -1236,7 +1296,10 @@ int seg_ck(int C, int ckmax) {
 }
 
 CUtensorMapSwizzle swizzle_pitch(uint32_t pitch) {
-    return pitch == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : pitch == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+    return pitch == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+           : pitch == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+           : pitch == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                         : CU_TENSOR_MAP_SWIZZLE_NONE;
 }
 
 CUtensorMapSwizzle swizzle_for(int kc) {
@@ -1261,9 +1324,12 @@ int g_host_err = 0;  // host-side failure of a launch: 4 tensor map, 8 no FP8 co
 
 bool tc_available() { return true; }
 
-// Channels a layer's first source carries in the tensor-core layout (the RGBDA input is
-// padded to 16 so that every K chunk is one 32-byte MMA step).
-static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 16 : L.cin0; }
+// Channels a layer's first source carries in the tensor-core layout: the RGBDA input is
+// padded to 8 (16 bytes per pixel; the halo kernel pairs taps for it, see issue_paired).
+static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 8 : L.cin0; }
+// The first conv: 8-channel input, halo kernel with tap pairs (the generic kernel needs
+// K chunks of at least 16 channels).
+static bool tc_paired(const ConvLayer& L) { return L.cin0 == 5 && !L.cin1; }
 
 static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax);
 
@@ -1398,7 +1464,12 @@ static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 //    [cx=0 dxc=-1], 16 per chunk.
 static std::vector<uint16_t> halo_blocks(const ConvLayer& L, int sg) {
     std::vector<uint16_t> b;
-    if (!L.cin1) {
+    if (tc_paired(L)) {  // [pair][half][ky = 2, 1, 0]: pair 0 = (kx 0 | kx 1), pair 1 = (zero | kx 2)
+        const int kxs[2][2] = {{0, 1}, {-1, 2}};
+        for (const auto& pr : kxs)
+            for (int kx : pr)
+                for (int ky = 2; ky >= 0; --ky) b.push_back(kx < 0 ? (uint16_t)0 : (uint16_t)(1u << (3 * ky + kx)));
+    } else if (!L.cin1) {
         for (int j = 0; j < 9; ++j) b.push_back((uint16_t)(1u << ((2 - j % 3) * 3 + j / 3)));
     } else if (sg == 0) {
         for (int t = 0; t < 9; ++t) b.push_back((uint16_t)(1u << t));
@@ -1510,7 +1581,7 @@ cudaError_t tc_prepare_fp8(ConvLayer& L) {
 
 // Weight blocks staged per chunk: 9, or for the nearest-upsampled operand of a decoder
 // concat conv 16 (all four classes) or the 8 of the tile's y class.
-static int halo_bload(int kind, int P) { return kind == 2 ? (P == 4 ? 16 : 8) : 9; }
+static int halo_bload(const ConvLayer& L, int kind, int P) { return tc_paired(L) ? 12 : kind == 2 ? (P == 4 ? 16 : 8) : 9; }
 
 // Parity-class tiles stack the two x classes along N (MMAs of 2N columns, at most 256).
 static bool halo_parity_ok(const ConvLayer& L, int P) { return P == 1 || (P >= 2 && 2 * L.cout <= 256); }
@@ -1526,7 +1597,7 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
-        const int bl = halo_bload(kind, P);
+        const int bl = halo_bload(L, kind, P);
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)bl * L.cout * pitch, 1024));
     }
     return st;
@@ -1535,9 +1606,14 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
 // Default halo tile of a layer: the most pixels per tile (P parity classes x R rows x 128
 // columns) whose P*R*N accumulator columns fit TMEM twice (even R when the layer pools),
 // then the widest chunk (64, then 32 channels) that leaves two pipeline stages; 16-channel
-// chunks only as a last resort.
+// chunks only as a last resort.  LNR_CONV_TMEM1=1: tiles whose accumulators fit TMEM once
+// (single-buffered), for tests of that variant.
 void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
     const int N = L.cout;
+    static const int nbuf = [] {
+        const char* e = getenv("LNR_CONV_TMEM1");
+        return e && atoi(e) == 1 ? 1 : 2;
+    }();
     const int Ps[3] = {4, 2, 1};
     for (int pass = 0; pass < 2; ++pass)
         for (int area = 8; area >= 1; area /= 2)
@@ -1545,7 +1621,7 @@ void halo_default(const ConvLayer& L, int& R, int& P, int& ckmax) {
                 const int pp = L.cin1 ? Ps[pi] : 1;
                 if (area % pp) continue;
                 const int r = area / pp;
-                if (2 * area * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, pp))) continue;
+                if (nbuf * area * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, pp))) continue;
                 const int cks[2] = {64, 32};
                 for (int i = 0; i < (pass ? 1 : 2); ++i) {
                     const int ck = pass ? 16 : cks[i];
@@ -1598,7 +1674,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     if (!L.cin1) P = 0;
     else if ((P != 1 && P != 2 && P != 4) || !halo_parity_ok(L, P)) return false;
     const int NC = P ? P : 1;
-    if ((R != 1 && R != 2 && R != 4 && R != 8) || 2 * NC * R * N > 512 || (L.pool && (R & 1))) return false;
+    if ((R != 1 && R != 2 && R != 4 && R != 8) || NC * R * N > 512 || (L.pool && (R & 1))) return false;
     p.N = N; p.W = W; p.H = H; p.B = B; p.R = R;
     p.parity = P;
     p.wmax = std::max(1, std::min(3, 256 / N));
@@ -1613,15 +1689,16 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.kind = kind;
         s.ck = seg_ck(C, ckmax);
         s.pitch = (uint32_t)s.ck * esize;
-        s.swz = s.pitch == 128 ? 2u : s.pitch == 64 ? 4u : 6u;
+        s.swz = s.pitch == 128 ? 2u : s.pitch == 64 ? 4u : s.pitch == 32 ? 6u : 0u;
+        s.paired = tc_paired(L) ? 1 : 0;
         s.rows = kind == 1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2;
         s.nchunk = C / s.ck;
         const uint32_t planes = kind == 1 ? 2 : 1;
         s.plane = align_up((uint32_t)s.rows * kHaloW * s.pitch, 1024);
         s.a_bytes = planes * (uint32_t)s.rows * kHaloW * s.pitch;
         s.b_off = planes * s.plane;
-        s.wblk = kind == 2 ? 16 : 9;
-        s.bload = halo_bload(kind, P);
+        s.wblk = s.paired ? 12 : kind == 2 ? 16 : 9;
+        s.bload = halo_bload(L, kind, P);
         s.bsel = kind == 2 && P != 4;
         const uint32_t b_bytes = (uint32_t)s.bload * N * s.pitch;
         s.bytes = s.a_bytes + b_bytes;
@@ -1723,8 +1800,9 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         g_host_err = 4;
         return true;
     }
+    p.tbufs = 2 * NC * R * N <= 512 ? 2 : 1;
     uint32_t cols = 32;
-    while (cols < 2u * NC * R * N) cols <<= 1;
+    while (cols < (uint32_t)(p.tbufs * NC * R * N)) cols <<= 1;
     p.tmem_cols = cols;
     // D = FP32; operands BF16 (format 1, kind::f16) or E4M3 (format 0, kind::f8f6f4)
     p.idesc = (1u << 4) | (ty.in8 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(N >> 3) << 17) |
@@ -1746,7 +1824,18 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     p.head_out = head_out;
     p.head_o = head_o;
     p.err = g_err;
-    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 6) + 16;
+    const size_t smem = 1024 + (size_t)p.stages * p.stage_bytes + stg_total + 8 * (2 * p.stages + 7) + 16;
+    p.wait_cycles = kWaitCycles;
+    // LNR_TEST_STALL_ONCE=1: the first halo launch of the process waits on a barrier nothing
+    // arrives on and gives up after ~1 ms (the test of the bounded waits and LNR_E_TIMEOUT)
+    static std::atomic<int> stall_once{[] {
+        const char* e = getenv("LNR_TEST_STALL_ONCE");
+        return e && atoi(e) == 1 ? 1 : 0;
+    }()};
+    if (stall_once.exchange(0)) {
+        p.stall = 1;
+        p.wait_cycles = 2000000ll;
+    }
     const int grid = std::min(p.ntiles, g_num_sms);
     auto launch = [&](void (*kern)(HParams), int threads) {
         static std::mutex mu;
@@ -1828,7 +1917,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     } else if (forced == 2) {
         cfg.mode = 2;
     }
-    if (fp8 && cfg.mode == 2) cfg.mode = 0;  // the generic kernel is BF16 only
+    if ((fp8 || tc_paired(L)) && cfg.mode == 2) cfg.mode = 0;  // the generic kernel: BF16, K chunks >= 16
     if (cfg.mode != 2) {
         int R = cfg.R, P = cfg.P, CK = cfg.CK;
         if (cfg.mode == 0) {
@@ -1859,11 +1948,12 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
 
 // Every valid kernel configuration of a layer: the generic kernel, and the halo kernel over
 // tile heights, parity classes per tile and chunk widths that fit TMEM (double-buffered
-// accumulators) and at least two pipeline stages.
+// accumulators, or single-buffered ones for tiles of up to 512 accumulator columns) and at
+// least two pipeline stages.
 std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
     std::vector<TcConfig> out;
     const bool in8 = prec == LNR_FP8 && L.fp8;
-    if (prec != LNR_FP8) {
+    if (prec != LNR_FP8 && !tc_paired(L)) {
         TcConfig g;
         g.mode = 2;
         out.push_back(g);
@@ -1873,7 +1963,7 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
     for (int r : {1, 2, 4, 8})
         for (int pi = 0; pi < (L.cin1 ? 3 : 1); ++pi) {
             const int P = L.cin1 ? Ps[pi] : 0, NC = P ? P : 1;
-            if (2 * NC * r * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, P))) continue;
+            if (NC * r * N > 512 || (L.pool && (r & 1)) || (L.cin1 && !halo_parity_ok(L, P))) continue;
             int last_ck[2] = {-1, -1};
             for (int ck : {16, 32, 64, 128}) {
                 if (ck * esize > 128 || (in8 && ck < 32)) continue;

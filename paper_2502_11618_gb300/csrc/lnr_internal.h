@@ -109,8 +109,10 @@ struct DBuf {
 
 struct GraphKey {
     int B, W, H, nlev, prec;
+    int vk;            // pinned view block the graph uploads from
+    const void* out;   // where the graph's U-Net head writes
     bool operator<(const GraphKey& o) const {
-        return std::tie(B, W, H, nlev, prec) < std::tie(o.B, o.W, o.H, o.nlev, o.prec);
+        return std::tie(B, W, H, nlev, prec, vk, out) < std::tie(o.B, o.W, o.H, o.nlev, o.prec, o.vk, o.out);
     }
 };
 
@@ -119,7 +121,7 @@ struct Workspace {
     int B = 0, W = 0, H = 0, nlev = 0;
     DBuf view;                              // ViewDev[B]
     DBuf cull_flag, cull_cnt, cull_bsum;    // per-cell temporaries
-    DBuf vis_cell, vis_pref, vis_tot;       // compacted visible cells, point prefix, totals
+    DBuf vis_info, vis_pref, vis_tot;       // visible cells (camera-space origin, position offset), point prefix, totals
     DBuf chunk_cell;                        // per view: first visible cell of every splat chunk
     DBuf keys;                              // uint64 [B][P]
     bool keys_dirty = true;
@@ -130,7 +132,14 @@ struct Workspace {
     DBuf u0;                                // float [B][P] kept depth (stage tap)
     DBuf act[4 * kMaxUnetLevels + 2];       // U-Net activations; [4 * kMaxUnetLevels] = U-Net input
     DBuf out;                               // float [B][P][3]
-    DBuf pinned_view;                       // host pinned ViewDev[B]
+    float* out_ptr = nullptr;               // U-Net output of the next frame: a caller's device buffer, or null for out
+    // View parameters go up from two pinned host blocks in turn; view_ev[k] is recorded right
+    // after block k's upload, so composing the next frame waits only for the upload that
+    // last used its block, never for the frame still on the device.
+    DBuf pinned_view[2];                    // host pinned ViewDev[B]
+    cudaEvent_t view_ev[2] = {nullptr, nullptr};
+    int vk = 0;                             // block of the frame being prepared
+    uint64_t vcount = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[16] = {nullptr};
     // CUDA graphs of whole frames, per (B, W, H, nlev, precision); valid while no buffer
@@ -139,6 +148,7 @@ struct Workspace {
     std::set<GraphKey> graph_warm;
     uint64_t alloc_gen = 0, graph_gen = 0, graph_cloud = 0, graph_unet = 0;
     void release();
+    size_t device_bytes() const;            // device memory held by the buffers above
 };
 
 struct Request {
@@ -219,7 +229,7 @@ size_t splat_max_chunks(uint64_t npoints);  // entries per view of the splat's c
 void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,
                            cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
-// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC16, 2 = none (stage taps only).
+// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC8, 2 = none (stage taps only).
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,
                      bool write_u0, cudaStream_t st);
 size_t pyramid_floats(int W, int H, int nlev);
@@ -232,10 +242,10 @@ cudaError_t probe_atomic_rate(uint64_t n_slots, uint64_t n_ops, int coherent, in
 lnr_status check_frame_args(lnr_ctx* c, int nviews, const lnr_view* views, const lnr_intrinsics* in, int W, int H,
                             int nlev, const float* fs, bool need_unet);
 lnr_status prepare_views(lnr_ctx* c, Workspace& ws, int B, const lnr_view* views, const lnr_intrinsics* in, int W,
-                         int H, int nlev, const float* fs);
+                         int H, int nlev, const float* fs, lnr_precision prec);
 void enqueue_frame(lnr_ctx* c, Workspace& ws, cudaStream_t st, int stage, lnr_precision prec, bool timed);
 cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph);
-size_t frame_bytes(int B, int W, int H, bool soft);  // raster workspace bytes of a batch
+size_t frame_bytes(const lnr_ctx* c, int B, int W, int H, bool soft);  // raster workspace bytes of a batch
 
 // unet.cu
 lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps);
@@ -246,6 +256,7 @@ lnr_status unet_prepare(lnr_ctx* c);
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
                   cudaStream_t st, cudaEvent_t* layer_ev);
 int unet_in_kind(lnr_precision p);
+size_t unet_in_bytes_per_px(lnr_precision p);  // network-input buffer bytes per pixel (the FP32 layout)
 
 // conv_tc.cu
 bool tc_available();

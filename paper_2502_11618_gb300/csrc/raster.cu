@@ -29,7 +29,7 @@ constexpr int kCullThreads = 256;
 constexpr int kCullPer = 4;
 constexpr int kCullTile = kCullThreads * kCullPer;
 constexpr int kSplatThreads = 256;
-constexpr int kSplatChunk = 2048;
+constexpr int kSplatChunk = 1024;  // visible points per splat range (one warp's unit of work)
 constexpr uint64_t kEmpty = ~0ull;
 
 __device__ __forceinline__ void cell_cam(int64_t i, int64_t j, int64_t k, const ViewDev& v, float o[3]) {
@@ -179,15 +179,16 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_scan(uint32_t* __restrict
     }
 }
 
-// Phase 3: compaction.  vis_cell[view][r] = cell id, vis_pref[view][r] = visible points
-// before it, and chunk_cell[view][k] = r for every splat chunk k (kSplatChunk visible
-// points) whose first point lies in this cell, so that the splat finds a chunk's cells
-// without searching.
-__global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ cnt,
-                               const uint32_t* __restrict__ bsum, int nb, int64_t C,
-                               const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ vis_cell,
-                               uint32_t* __restrict__ vis_pref, uint32_t* __restrict__ chunk_cell,
-                               size_t max_chunks) {
+// Phase 3: compaction.  For the r-th visible cell of a view: vis_info[view][r] = its
+// camera-space origin and (sorted position of its first point - visible points before it),
+// vis_pref[view][r] = visible points before it; and chunk_cell[view][k] = r for every
+// splat range k (kSplatChunk visible points) whose first point lies in this cell, so that
+// the splat finds a range's cells without searching.
+__global__ void k_cull_compact(const ViewDev* __restrict__ views, const uint32_t* __restrict__ flag,
+                               const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ bsum, int nb,
+                               int64_t C, int dx, int dy, const uint32_t* __restrict__ cell_start,
+                               float4* __restrict__ vis_info, uint32_t* __restrict__ vis_pref,
+                               uint32_t* __restrict__ chunk_cell, size_t max_chunks) {
     const int view = blockIdx.y;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
@@ -197,7 +198,9 @@ __global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t
     const uint32_t* bs = bsum + ((size_t)view * nb + b) * 2;
     uint32_t r = bs[0] + f;
     const uint32_t pref = bs[1] + cnt[(size_t)view * C + c];
-    vis_cell[(size_t)view * C + r] = (uint32_t)c;
+    float o[3];
+    cell_cam(c % dx, (c / dx) % dy, c / ((int64_t)dx * dy), views[view], o);
+    vis_info[(size_t)view * C + r] = make_float4(o[0], o[1], o[2], __uint_as_float(cell_start[c] - pref));
     vis_pref[(size_t)view * C + r] = pref;
     const uint32_t n = cell_start[c + 1] - cell_start[c];  // > 0: only non-empty cells are visible
     uint32_t* cc = chunk_cell + (size_t)view * max_chunks;
@@ -205,115 +208,138 @@ __global__ void k_cull_compact(const uint32_t* __restrict__ flag, const uint32_t
 }
 
 // ------------------------------------------------------------------ splat ----
+//
+// Warps work independently (no block barriers) through ranges of kSplatChunk consecutive
+// visible points, the ranges of all views of the batch in one list.  For a range, lane l
+// holds visible cell (first cell of the range) + l: its camera-space origin, the offset
+// from visible-point index to sorted position and its point prefix, loaded from the
+// compaction's tables.  The points are taken 32 x kSplatBatch at a time (a batch); a
+// batch's cells are the lanes from the one holding its first point on, found with warp
+// votes: when the whole batch lies in one cell (the common case) every lane takes that
+// cell's data with warp-uniform shuffles, else each point compares its index with the
+// prefixes of the few cells that start inside the batch.  A range whose points span more
+// than 32 cells is processed 32 cells at a time.  Each lane keeps kSplatBatch points'
+// offset loads in flight before projecting them.  The views' parameters are staged in
+// shared memory once per block.
 
-// Splat loads in flight per thread: kSplatBatch points' offsets are fetched before any of
-// them is projected (the pass is bound by load latency, not bandwidth).
 constexpr int kSplatBatch = 4;
+constexpr int kSplatMaxViews = 64;  // views per launch (their parameters are staged in shared memory)
 
-// SOFT = false: hard z-buffer pass, atomicMin of (bits(z) << 32 | position) per pixel.
-// SOFT = true: second pass of the soft z-buffer (Sec. 3: colours of points arriving at
-// similar depths are averaged): every point whose depth is within z_front * scale (one
-// FP32 multiply) of its pixel's front, read from the finished keys, adds its colour and a
-// count to the pixel's integer sums -- acc[2q] = r << 32 | g, acc[2q+1] = b << 32 | n --
-// so the result does not depend on the order of the atomics.
 template <bool SOFT>
 __global__ void __launch_bounds__(kSplatThreads, 4) k_splat(
-    const ViewDev* __restrict__ views, const uint32_t* __restrict__ cell_start, int dx, int dy,
-    int64_t C, const uint32_t* __restrict__ vis_cell, const uint32_t* __restrict__ vis_pref,
-    const uint32_t* __restrict__ tot, const float* __restrict__ ox, const float* __restrict__ oy,
-    const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys,
+    const ViewDev* __restrict__ views, int nviews, int64_t C, const float4* __restrict__ vis_info,
+    const uint32_t* __restrict__ vis_pref, const uint32_t* __restrict__ tot, const float* __restrict__ ox,
+    const float* __restrict__ oy, const float* __restrict__ oz, int W, int H, unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ rgbs, unsigned long long* __restrict__ acc, float scale,
     const uint32_t* __restrict__ chunk_cell, size_t max_chunks, uint32_t pos_base) {
-    // per chunk cell: camera-space origin + (sorted position of its first point - pref),
-    // and pref = visible points before it (a separate array: 20 KB + 8 KB keeps five
-    // blocks per SM)
-    __shared__ float4 cells[kSplatChunk];
-    __shared__ uint32_t cpref[kSplatChunk];
-    const int view = blockIdx.y;
-    const ViewDev v = views[view];
-    const uint32_t nvc = tot[2 * view], npts = tot[2 * view + 1];
-    const uint32_t* vc = vis_cell + (size_t)view * C;
-    const uint32_t* vp = vis_pref + (size_t)view * C;
-    unsigned long long* kv = keys + (size_t)view * W * H;
+    __shared__ ViewDev sv[kSplatMaxViews];
+    for (int i = threadIdx.x; i < nviews * (int)(sizeof(ViewDev) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(sv)[i] = reinterpret_cast<const uint32_t*>(views)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;  // lanes before this one
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const float Wf = (float)W, Hf = (float)H;
-    for (uint64_t chunk = blockIdx.x;; chunk += gridDim.x) {
-        uint64_t start = chunk * kSplatChunk;
-        if (start >= npts) break;
-        uint32_t end = (uint32_t)(start + kSplatChunk < (uint64_t)npts ? start + kSplatChunk : (uint64_t)npts);
-        // first cell: the one holding point `start`; last: the one holding point end - 1
-        const uint32_t* ck = chunk_cell + (size_t)view * max_chunks;
-        const int vc0 = (int)ck[chunk];
-        int vc1 = (int)nvc - 1;
-        if (end < npts) {
-            vc1 = (int)ck[chunk + 1];
-            if (vp[vc1] >= end) --vc1;
+    int view = 0;
+    uint64_t first = 0;  // global index of the view's first range
+    for (uint64_t g = warp0;; g += nwarps) {
+        // the view of global range g (ranges of view 0 first, then view 1, ...)
+        uint32_t nr = (tot[2 * view + 1] + kSplatChunk - 1) / kSplatChunk;
+        while (g >= first + nr) {
+            first += nr;
+            if (++view == nviews) return;
+            nr = (tot[2 * view + 1] + kSplatChunk - 1) / kSplatChunk;
         }
-        const int nc = vc1 - vc0 + 1;
-        for (int t = threadIdx.x; t < nc; t += kSplatThreads) {
-            uint32_t c = vc[vc0 + t];
-            int64_t i = c % (uint32_t)dx, j = (c / (uint32_t)dx) % (uint32_t)dy, k = c / ((uint32_t)dx * (uint32_t)dy);
-            float o[3];
-            cell_cam(i, j, k, v, o);
-            const uint32_t pref = vp[vc0 + t];
-            cells[t] = make_float4(o[0], o[1], o[2], __uint_as_float(cell_start[c] - pref));
-            cpref[t] = pref;
-        }
-        __syncthreads();
-        int cur = 0;
-        for (uint32_t e0 = (uint32_t)start + threadIdx.x; e0 < end; e0 += kSplatBatch * kSplatThreads) {
-            float px[kSplatBatch], py[kSplatBatch], pz[kSplatBatch];
-            uint32_t pos[kSplatBatch];
-            int cell[kSplatBatch];
-#pragma unroll
-            for (int b = 0; b < kSplatBatch; ++b) {
-                const uint32_t e = e0 + b * kSplatThreads;
-                cell[b] = -1;
-                if (e >= end) continue;
-                // the cell of element e: last chunk cell with pref <= e (elements increase)
-                int lo = cur, hi = nc - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (cpref[mid] <= e) lo = mid; else hi = mid - 1;
-                }
-                cur = lo;
-                cell[b] = lo;
-                pos[b] = e + __float_as_uint(cells[lo].w);
-                px[b] = ox[pos[b]];
-                py[b] = oy[pos[b]];
-                pz[b] = oz[pos[b]];
+        const ViewDev& v = sv[view];
+        const uint32_t nvc = tot[2 * view], npts = tot[2 * view + 1];
+        const float4* vi = vis_info + (size_t)view * C;
+        const uint32_t* vp = vis_pref + (size_t)view * C;
+        unsigned long long* kv = keys + (size_t)view * W * H;
+        const uint32_t rg = (uint32_t)(g - first);
+        const uint32_t start = rg * kSplatChunk;
+        const uint32_t end = min(start + (uint32_t)kSplatChunk, npts);
+        uint32_t cb = chunk_cell[(size_t)view * max_chunks + rg];  // the cell holding point `start`
+        for (uint32_t a = start; a < end;) {
+            // lane l: visible cell cb + l
+            const uint32_t k = cb + (uint32_t)lane;
+            float4 info = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t pref = 0xffffffffu;
+            if (k < nvc) {
+                info = vi[k];
+                pref = vp[k];
             }
+            // points [a, b) lie in these 32 cells
+            const uint32_t b = min(end, cb + 32 < nvc ? vp[cb + 32] : 0xffffffffu);
+            for (uint32_t e0 = a; e0 < b; e0 += 32 * kSplatBatch) {
+                const uint32_t elast = min(e0 + 32 * kSplatBatch, b) - 1;
+                // the lane of the cell holding e0, and the cells starting later in the batch
+                const int cur = __popc(__ballot_sync(0xffffffffu, pref <= e0)) - 1;
+                const uint32_t starts = __ballot_sync(0xffffffffu, pref > e0 && pref <= elast);
+                float px[kSplatBatch], py[kSplatBatch], pz[kSplatBatch];
+                uint32_t pos[kSplatBatch];
+                int cl[kSplatBatch];
+                const uint32_t off0 = __float_as_uint(__shfl_sync(0xffffffffu, info.w, cur));
 #pragma unroll
-            for (int b = 0; b < kSplatBatch; ++b) {
-                if (cell[b] < 0) continue;
-                const float4 co = cells[cell[b]];
-                const float cell_o[3] = {co.x, co.y, co.z};
-                float p[3];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    float t = __fmaf_rn(v.Rf[3 * r + 2], pz[b], cell_o[r]);
-                    t = __fmaf_rn(v.Rf[3 * r + 1], py[b], t);
-                    p[r] = __fmaf_rn(v.Rf[3 * r + 0], px[b], t);
+                for (int t = 0; t < kSplatBatch; ++t) {
+                    const uint32_t e = e0 + (uint32_t)(32 * t + lane);
+                    cl[t] = cur;
+                    uint32_t off = off0;
+                    if (starts) {  // warp-uniform: some cell starts inside the batch
+                        for (uint32_t m = starts; m; m &= m - 1) {
+                            const int j = __ffs(m) - 1;
+                            if (__shfl_sync(0xffffffffu, pref, j) <= e) cl[t] = j;
+                        }
+                        off = __float_as_uint(__shfl_sync(0xffffffffu, info.w, cl[t]));
+                    }
+                    pos[t] = e + off;
+                    if (e <= elast) {
+                        px[t] = ox[pos[t]];
+                        py[t] = oy[pos[t]];
+                        pz[t] = oz[pos[t]];
+                    }
                 }
-                const float z = p[2];
-                if (!(z > v.znear && z < v.zfar)) continue;
-                const float u = __fadd_rn(__fdiv_rn(__fmul_rn(v.fx, p[0]), z), v.cx);
-                const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
-                if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
-                const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
-                if (!SOFT) {
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (pos[b] + pos_base);
-                    atomicMin(&kv[pix], key);
-                } else {
-                    const unsigned long long front = kv[pix];
-                    if (front == kEmpty || !(z <= __fmul_rn(__uint_as_float((uint32_t)(front >> 32)), scale))) continue;
-                    const uint32_t col = rgbs[pos[b]];
-                    unsigned long long* a = acc + 2 * ((size_t)view * W * H + pix);
-                    atomicAdd(a, ((unsigned long long)(col & 255u) << 32) | ((col >> 8) & 255u));
-                    atomicAdd(a + 1, ((unsigned long long)((col >> 16) & 255u) << 32) | 1ull);
+                float c0u = __shfl_sync(0xffffffffu, info.x, cur), c1u = __shfl_sync(0xffffffffu, info.y, cur),
+                      c2u = __shfl_sync(0xffffffffu, info.z, cur);
+#pragma unroll
+                for (int t = 0; t < kSplatBatch; ++t) {
+                    float c0 = c0u, c1 = c1u, c2 = c2u;
+                    if (starts) {
+                        c0 = __shfl_sync(0xffffffffu, info.x, cl[t]);
+                        c1 = __shfl_sync(0xffffffffu, info.y, cl[t]);
+                        c2 = __shfl_sync(0xffffffffu, info.z, cl[t]);
+                    }
+                    if (e0 + (uint32_t)(32 * t + lane) > elast) continue;
+                    const float cell_o[3] = {c0, c1, c2};
+                    float p[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        float q = __fmaf_rn(v.Rf[3 * r + 2], pz[t], cell_o[r]);
+                        q = __fmaf_rn(v.Rf[3 * r + 1], py[t], q);
+                        p[r] = __fmaf_rn(v.Rf[3 * r + 0], px[t], q);
+                    }
+                    const float z = p[2];
+                    if (!(z > v.znear && z < v.zfar)) continue;
+                    const float u = __fadd_rn(__fdiv_rn(__fmul_rn(v.fx, p[0]), z), v.cx);
+                    const float w = __fadd_rn(__fdiv_rn(__fmul_rn(v.fy, p[1]), z), v.cy);
+                    if (!(u >= 0.0f && u < Wf && w >= 0.0f && w < Hf)) continue;
+                    const int64_t pix = (int64_t)floorf(w) * W + (int64_t)floorf(u);
+                    if (!SOFT) {
+                        const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (pos[t] + pos_base);
+                        atomicMin(&kv[pix], key);
+                    } else {
+                        const unsigned long long front = kv[pix];
+                        if (front == kEmpty || !(z <= __fmul_rn(__uint_as_float((uint32_t)(front >> 32)), scale))) continue;
+                        const uint32_t col = rgbs[pos[t]];
+                        unsigned long long* ac = acc + 2 * ((size_t)view * W * H + pix);
+                        atomicAdd(ac, ((unsigned long long)(col & 255u) << 32) | ((col >> 8) & 255u));
+                        atomicAdd(ac + 1, ((unsigned long long)((col >> 16) & 255u) << 32) | 1ull);
+                    }
                 }
             }
+            a = b;
+            cb += 32;
         }
-        __syncthreads();
     }
 }
 
@@ -417,7 +443,7 @@ struct UpArgs {
     int fill;            // non-final level: fill empty pixels by interpolation
     // final level only
     const uint32_t* rgba;
-    void* unet_in;       // NHWC: 8 FP32 channels (kind 0) or 16 BF16 channels (kind 1)
+    void* unet_in;       // NHWC: 8 FP32 channels (kind 0) or 8 BF16 channels (kind 1)
     int kind;            // 0 = FP32, 1 = BF16, 2 = none
     float* u0;           // kept depth tap (nullable)
 };
@@ -430,7 +456,8 @@ __device__ __forceinline__ void st_sector(void* dst, uint32_t w0, uint32_t w1, u
                  : "memory");
 }
 
-// One pixel of the network input (32 bytes in both layouts), written as one sector.
+// One pixel of the network input: 8 FP32 channels (32 bytes, one sector) or 8 BF16
+// channels (16 bytes), written with one store.
 __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, float r, float g, float b,
                                               float d, float a) {
     if (kind == 0) {
@@ -439,8 +466,8 @@ __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, fl
     } else if (kind == 1) {
         __nv_bfloat162 v0 = __floats2bfloat162_rn(r, g), v1 = __floats2bfloat162_rn(b, d);
         __nv_bfloat162 v2 = __floats2bfloat162_rn(a, 0.f);
-        st_sector(static_cast<uint4*>(base) + 2 * q, *reinterpret_cast<uint32_t*>(&v0), *reinterpret_cast<uint32_t*>(&v1),
-                  *reinterpret_cast<uint32_t*>(&v2), 0u, 0u, 0u, 0u, 0u);
+        static_cast<uint4*>(base)[q] = make_uint4(*reinterpret_cast<uint32_t*>(&v0), *reinterpret_cast<uint32_t*>(&v1),
+                                                  *reinterpret_cast<uint32_t*>(&v2), 0u);
     }
 }
 
@@ -549,7 +576,7 @@ __global__ void k_extract5(const void* in, int kind, float* out, int64_t npx) {
     for (int c = 0; c < 5; ++c) {
         float v;
         if (kind == 0) v = static_cast<const float*>(in)[q * 8 + c];
-        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 16 + c]);
+        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 8 + c]);
         out[q * 5 + c] = v;
     }
 }
@@ -569,22 +596,41 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                               ws.cull_bsum.as<uint32_t>(), nb);
     k_cull_scan<<<ws.B, kCullThreads, 0, st>>>(ws.cull_bsum.as<uint32_t>(), nb, ws.vis_tot.as<uint32_t>());
     dim3 g3((unsigned)((c->ncells + 255) / 256), ws.B);
-    k_cull_compact<<<g3, 256, 0, st>>>(ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
-                                       ws.cull_bsum.as<uint32_t>(), nb, c->ncells, c->cell_start.as<uint32_t>(),
-                                       ws.vis_cell.as<uint32_t>(), ws.vis_pref.as<uint32_t>(),
+    k_cull_compact<<<g3, 256, 0, st>>>(ws.view.as<ViewDev>(), ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
+                                       ws.cull_bsum.as<uint32_t>(), nb, c->ncells, c->dims[0], c->dims[1],
+                                       c->cell_start.as<uint32_t>(), ws.vis_info.as<float4>(), ws.vis_pref.as<uint32_t>(),
                                        ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
 }
 
-void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
-    int per_view = std::max(1, (c->num_sms * 8) / ws.B);
-    dim3 g(per_view, ws.B);
-    k_splat<false><<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
-                                                c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
-                                                ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
-                                                c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
-                                                ws.keys.as<unsigned long long>(), nullptr, nullptr, 1.0f,
-                                                ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n), c->shard_base);
+// Grid of the splat: as many blocks as fit on the GPU at once (the warps stride through the
+// ranges of every view).
+static int splat_blocks(const lnr_ctx* c, bool soft) {
+    static int per_sm[2] = {0, 0};
+    if (!per_sm[soft]) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, soft ? k_splat<true> : k_splat<false>, kSplatThreads, 0);
+        per_sm[soft] = std::max(1, n);
+    }
+    return c->num_sms * per_sm[soft];
 }
+
+// One launch per group of up to kSplatMaxViews views.
+template <bool SOFT>
+static void splat_views(const lnr_ctx* c, Workspace& ws, cudaStream_t st, float scale) {
+    const size_t P = (size_t)ws.W * ws.H, mc = splat_max_chunks(c->n);
+    for (int v0 = 0; v0 < ws.B; v0 += kSplatMaxViews) {
+        const int nv = std::min(kSplatMaxViews, ws.B - v0);
+        k_splat<SOFT><<<splat_blocks(c, SOFT), kSplatThreads, 0, st>>>(
+            ws.view.as<ViewDev>() + v0, nv, c->ncells, ws.vis_info.as<float4>() + (size_t)v0 * c->ncells,
+            ws.vis_pref.as<uint32_t>() + (size_t)v0 * c->ncells,
+            ws.vis_tot.as<uint32_t>() + 2 * v0, c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
+            ws.keys.as<unsigned long long>() + v0 * P, SOFT ? c->rgbs.as<uint32_t>() : nullptr,
+            SOFT ? ws.soft_acc.as<unsigned long long>() + 2 * v0 * P : nullptr, scale,
+            ws.chunk_cell.as<uint32_t>() + (size_t)v0 * mc, mc, SOFT ? 0u : c->shard_base);
+    }
+}
+
+void launch_splat(const lnr_ctx* c, Workspace& ws, cudaStream_t st) { splat_views<false>(c, ws, st, 1.0f); }
 
 // Second pass of the soft z-buffer (after launch_splat has finished the keys).
 void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
@@ -592,16 +638,7 @@ void launch_splat_soft(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
         cudaMemsetAsync(ws.soft_acc.p, 0, ws.soft_acc.bytes, st);
         ws.soft_dirty = false;
     }
-    int per_view = std::max(1, (c->num_sms * 8) / ws.B);
-    dim3 g(per_view, ws.B);
-    const float scale = 1.0f + c->soft_rel;
-    k_splat<true><<<g, kSplatThreads, 0, st>>>(ws.view.as<ViewDev>(), c->cell_start.as<uint32_t>(), c->dims[0],
-                                               c->dims[1], c->ncells, ws.vis_cell.as<uint32_t>(),
-                                               ws.vis_pref.as<uint32_t>(), ws.vis_tot.as<uint32_t>(),
-                                               c->ox.as<float>(), c->oy.as<float>(), c->oz.as<float>(), ws.W, ws.H,
-                                               ws.keys.as<unsigned long long>(), c->rgbs.as<uint32_t>(),
-                                               ws.soft_acc.as<unsigned long long>(), scale,
-                                               ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n), 0u);
+    splat_views<true>(c, ws, st, 1.0f + c->soft_rel);
 }
 
 // ------------------------------------------------------- atomic throughput probe ----

@@ -8,6 +8,13 @@
 // the batch (a replayed CUDA graph once the configuration has been seen) followed by the
 // device-to-host copy of every result into its own pinned buffer and an event.  Work of
 // different slots overlaps on the device.  Completed requests are picked up by lnr_poll.
+//
+// Memory: a slot's buffers grow to the largest batch it has run.  Under a budget
+// (lnr_set_memory_budget) admission counts the bytes the slots actually hold: a batch is
+// launched when the busy slots' buffers plus the batch's own need fit, and before the
+// launch the slot's buffers, then idle slots' buffers, are released while the total the
+// slots would hold exceeds the budget.  So the device memory of all slots stays within the
+// budget whenever one batch of one request fits in it.
 // Every wait is bounded: the scheduler polls events, and lnr_serve_stop gives the device a
 // deadline before reporting a timeout.
 #include <chrono>
@@ -21,7 +28,6 @@ struct Slot {
     Workspace ws;
     cudaEvent_t done = nullptr;
     std::vector<uint64_t> tickets;
-    size_t act_bytes = 0;
     bool busy = false;
 };
 
@@ -125,6 +131,8 @@ struct ServeReq {
     bool done = false, failed = false;
     float* host = nullptr;  // pinned result, H*W*3 floats
     size_t bytes = 0;
+    float* user = nullptr;  // lnr_submit_into: the caller's destination
+    bool user_pinned = false;  // ... page-locked: the result is copied straight into it
 };
 
 struct Server {
@@ -138,23 +146,50 @@ struct Server {
     std::thread th;
     std::atomic<bool> stop{false};
     uint64_t next_ticket = 1;
-    size_t inflight = 0;
     PinnedPool pool;
     CopyPool copier;
     lnr_precision prec = LNR_FP32;
     // stats
-    uint64_t n_done = 0, n_launch = 0, max_b = 0, peak_bytes = 0;
+    uint64_t n_done = 0, n_launch = 0, max_b = 0, peak_bytes = 0, peak_alloc = 0, peak_busy = 0;
     std::string err;
 
     void loop();
-    bool launch(Slot& s, std::vector<uint64_t>& batch);
+    bool launch(Slot& s, std::vector<uint64_t>& batch, size_t need);
+    size_t busy_bytes(const Slot* except) const;
+    void make_room(Slot& s, size_t need);
 };
 
+// Device bytes a batch of B requests of W x H needs: its U-Net activations and its raster
+// buffers (the network input and output included).
 static size_t request_bytes(const lnr_ctx* c, int B, int W, int H, lnr_precision p) {
-    return unet_act_bytes(c->unet, B, W, H, p) + frame_bytes(B, W, H, c->soft_rel > 0.0f);
+    return unet_act_bytes(c->unet, B, W, H, p) + frame_bytes(c, B, W, H, c->soft_rel > 0.0f);
 }
 
-bool Server::launch(Slot& s, std::vector<uint64_t>& batch) {
+size_t Server::busy_bytes(const Slot* except) const {
+    size_t n = 0;
+    for (const auto& sp : slots)
+        if (sp.get() != except && sp->busy) n += sp->ws.device_bytes();
+    return n;
+}
+
+// Under a budget: release this slot's buffers when they outgrow the batch, then idle slots'
+// buffers, while the slots together would hold more than the budget.
+void Server::make_room(Slot& s, size_t need) {
+    const size_t budget = c->mem_budget;
+    if (!budget) return;
+    auto total = [&] {
+        size_t n = 0;
+        for (const auto& sp : slots) n += sp.get() == &s ? std::max(sp->ws.device_bytes(), need) : sp->ws.device_bytes();
+        return n;
+    };
+    if (total() > budget && s.ws.device_bytes() > need) s.ws.release();
+    for (auto& sp : slots) {
+        if (total() <= budget) break;
+        if (sp.get() != &s && !sp->busy && sp->ws.device_bytes()) sp->ws.release();
+    }
+}
+
+bool Server::launch(Slot& s, std::vector<uint64_t>& batch, size_t need) {
     const int B = (int)batch.size();
     std::vector<lnr_view> views(B);
     std::vector<lnr_intrinsics> intr(B);
@@ -173,7 +208,14 @@ bool Server::launch(Slot& s, std::vector<uint64_t>& batch) {
         H = r0.H;
         nlev = r0.nlev;
     }
-    if (prepare_views(c, s.ws, B, views.data(), intr.data(), W, H, nlev, fs.data()) != LNR_OK) return false;
+    make_room(s, need);
+    if (prepare_views(c, s.ws, B, views.data(), intr.data(), W, H, nlev, fs.data(), prec) != LNR_OK) return false;
+    {
+        size_t held = 0;
+        for (const auto& sp : slots) held += sp->ws.device_bytes();
+        std::lock_guard<std::mutex> g(mu);
+        peak_alloc = std::max<uint64_t>(peak_alloc, held);
+    }
     if (run_frame(c, s.ws, prec, true) != cudaSuccess) return false;
     const size_t per = (size_t)W * H * 3;
     for (int i = 0; i < B; ++i) {
@@ -181,11 +223,13 @@ bool Server::launch(Slot& s, std::vector<uint64_t>& batch) {
         {
             std::lock_guard<std::mutex> g(mu);
             ServeReq& r = reqs[batch[i]];
-            if (!r.host) {
-                r.bytes = per * 4;
-                r.host = pool.get(r.bytes);
+            r.bytes = per * 4;
+            if (r.user_pinned) {
+                dst = r.user;
+            } else {
+                if (!r.host) r.host = pool.get(r.bytes);
+                dst = r.host;
             }
-            dst = r.host;
         }
         if (!dst || cudaMemcpyAsync(dst, s.ws.out.as<float>() + i * per, per * 4, cudaMemcpyDeviceToHost, s.ws.stream))
             return false;
@@ -217,7 +261,6 @@ void Server::loop() {
                 ++n_done;
             }
             if (q != cudaSuccess) err = cudaGetErrorString(q);
-            inflight -= s.act_bytes;
             s.busy = false;
             s.tickets.clear();
             progressed = true;
@@ -238,33 +281,35 @@ void Server::loop() {
                     if (r.W == h.W && r.H == h.H && r.nlev == h.nlev) take.push_back(i);
                 }
                 bytes = request_bytes(c, (int)take.size(), h.W, h.H, prec);
-                if (c->mem_budget && inflight > 0 && inflight + bytes > c->mem_budget) {
-                    // shrink the batch until it fits next to what is in flight
-                    while (take.size() > 1 && inflight + request_bytes(c, (int)take.size(), h.W, h.H, prec) > c->mem_budget)
+                const size_t busy = busy_bytes(&s);
+                if (c->mem_budget && busy > 0 && busy + bytes > c->mem_budget) {
+                    // shrink the batch until it fits next to the buffers of the busy slots
+                    while (take.size() > 1 && busy + request_bytes(c, (int)take.size(), h.W, h.H, prec) > c->mem_budget)
                         take.pop_back();
                     bytes = request_bytes(c, (int)take.size(), h.W, h.H, prec);
-                    if (inflight + bytes > c->mem_budget) break;  // wait for completions
+                    if (busy + bytes > c->mem_budget) break;  // wait for completions
                 }
                 for (size_t k = take.size(); k-- > 0;) {
                     batch.insert(batch.begin(), queue[take[k]]);
                     queue.erase(queue.begin() + (long)take[k]);
                 }
-                inflight += bytes;
-                peak_bytes = std::max<uint64_t>(peak_bytes, inflight);
+                peak_bytes = std::max<uint64_t>(peak_bytes, busy + bytes);
             }
-            s.act_bytes = bytes;
-            if (!launch(s, batch)) {
+            if (!launch(s, batch, bytes)) {
                 std::lock_guard<std::mutex> g(mu);
                 for (uint64_t tk : batch) {
                     reqs[tk].done = true;
                     reqs[tk].failed = true;
                 }
                 err = c->err.empty() ? "launch failed" : c->err;
-                inflight -= bytes;
                 s.busy = false;
             } else {
                 ++n_launch;
                 max_b = std::max<uint64_t>(max_b, batch.size());
+                uint64_t nb = 0;
+                for (const auto& sp : slots) nb += sp->busy ? 1 : 0;
+                std::lock_guard<std::mutex> g(mu);
+                peak_busy = std::max(peak_busy, nb);
             }
             progressed = true;
         }
@@ -345,6 +390,11 @@ lnr_status lnr_set_memory_budget(lnr_ctx* c, size_t bytes) {
 
 lnr_status lnr_submit(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* intr, int W, int H, int nlev, float fs,
                       uint64_t* ticket) {
+    return lnr_submit_into(c, view, intr, W, H, nlev, fs, nullptr, ticket);
+}
+
+lnr_status lnr_submit_into(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* intr, int W, int H, int nlev,
+                           float fs, float* out_rgb, uint64_t* ticket) {
     if (!c || !ticket) return LNR_E_ARG;
     Server* s = c->server;
     if (!s) return fail(c, LNR_E_STATE, "serving not started");
@@ -358,6 +408,12 @@ lnr_status lnr_submit(lnr_ctx* c, const lnr_view* view, const lnr_intrinsics* in
     r.H = H;
     r.nlev = nlev;
     r.fs = fs;
+    r.user = out_rgb;
+    if (out_rgb) {
+        cudaPointerAttributes at{};
+        r.user_pinned = cudaPointerGetAttributes(&at, out_rgb) == cudaSuccess && at.type == cudaMemoryTypeHost;
+        cudaGetLastError();  // a pageable pointer may leave an error behind
+    }
     r.t_submit = now_s();
     const uint64_t t = s->next_ticket++;
     s->reqs.emplace(t, r);
@@ -381,8 +437,10 @@ lnr_status lnr_poll(lnr_ctx* c, uint64_t ticket, float* out, double* latency_s) 
         s->reqs.erase(it);
     }
     lnr_status st = LNR_OK;
+    if (!out && !r.user_pinned) out = r.user;  // lnr_submit_into with a pageable destination
     if (r.failed) st = fail(c, LNR_E_CUDA, "request failed: " + s->err);
     else if (out && r.host) s->copier.copy(out, r.host, r.bytes);
+    else if (out && r.user_pinned && out != r.user) std::memcpy(out, r.user, r.bytes);
     if (latency_s) *latency_s = r.t_done - r.t_submit;
     if (r.host) {
         std::lock_guard<std::mutex> g(s->mu);
@@ -391,11 +449,11 @@ lnr_status lnr_poll(lnr_ctx* c, uint64_t ticket, float* out, double* latency_s) 
     return st;
 }
 
-lnr_status lnr_serve_stats(lnr_ctx* c, uint64_t out[4]) {
+lnr_status lnr_serve_stats(lnr_ctx* c, uint64_t out[6]) {
     if (!c || !out) return LNR_E_ARG;
     Server* s = c->server;
     if (!s) {
-        for (int i = 0; i < 4; ++i) out[i] = 0;
+        for (int i = 0; i < 6; ++i) out[i] = 0;
         return LNR_OK;
     }
     std::lock_guard<std::mutex> g(s->mu);
@@ -403,6 +461,8 @@ lnr_status lnr_serve_stats(lnr_ctx* c, uint64_t out[4]) {
     out[1] = s->n_launch;
     out[2] = s->max_b;
     out[3] = s->peak_bytes;
+    out[4] = s->peak_alloc;
+    out[5] = s->peak_busy;
     return LNR_OK;
 }
 

@@ -168,16 +168,20 @@ inline int slot(int l, int k) { return 4 * l + k; }
 }  // namespace
 
 int unet_in_kind(lnr_precision p) { return p == LNR_FP32 ? 0 : 1; }
+// Bytes per pixel of the network-input buffer: the FP32 layout (8 x 4 bytes), which the stage
+// taps use at every precision; the BF16 layout (8 x 2 bytes) fits in it.
+size_t unet_in_bytes_per_px(lnr_precision) { return 8 * 4; }
 
 static size_t elem_bytes(lnr_precision p) { return p == LNR_FP32 ? 4 : 2; }
 
+// Activation buffers of the forward pass (the network input and output are counted with the
+// frame's raster buffers): four per level, each at most the level's size (+ 256 bytes).
 size_t unet_act_bytes(const Unet& u, int B, int W, int H, lnr_precision p) {
-    size_t tot = (size_t)B * W * H * 8 * elem_bytes(p);  // input
+    size_t tot = 0;
     for (int l = 0; l < u.levels; ++l) {
         size_t Pl = (size_t)B * (W >> l) * (H >> l);
-        tot += Pl * u.ch[l] * elem_bytes(p) * 4;
+        tot += (Pl * u.ch[l] * elem_bytes(p) + 256) * 4;
     }
-    tot += (size_t)B * W * H * 3 * 4;  // output
     return tot;
 }
 
@@ -276,8 +280,40 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
     }
 }
 
+// FP8 policy.  Headroom of the static activation scales over the calibration frames'
+// largest magnitudes, and the convolutions that keep BF16 operands: the full-resolution
+// encoder convs (the first reads the BF16 RGBDA image) and every decoder conv at full and
+// half resolution (the last one's features feed the output head).  E4M3's three mantissa
+// bits cost the most accuracy there: on 16 1080p views keeping the second encoder conv in
+// BF16 raised the minimum PSNR by 0.8 dB, and on a small frame with other weights the
+// decoder's level-1 convs decided whether the 38 dB bar held.  Scale headroom between 2
+// and 64 changed nothing measurable (E4M3 is floating point).  LNR_FP8_HEADROOM and
+// LNR_FP8_BF16_LAYERS (comma-separated indices in network order, replacing the default
+// set) override them for measurements.
 constexpr float kFp8Headroom = 8.0f;
-constexpr bool kFp8Level0DecoderBf16 = false;
+
+static float fp8_headroom() {
+    const char* e = getenv("LNR_FP8_HEADROOM");
+    const float v = e ? (float)atof(e) : kFp8Headroom;
+    return v >= 1.0f && v <= 1e4f ? v : kFp8Headroom;
+}
+
+static bool fp8_layer_bf16(int layer, int level, bool decoder) {
+    static const char* env = getenv("LNR_FP8_BF16_LAYERS");
+    if (!env) return decoder ? level <= 1 : level == 0;
+    static const std::vector<int> keep = [] {
+        std::vector<int> v;
+        for (const char* p = env; p && *p;) {
+            v.push_back(atoi(p));
+            p = strchr(p, ',');
+            if (p) ++p;
+        }
+        return v;
+    }();
+    for (int k : keep)
+        if (k == layer) return true;
+    return false;
+}
 
 __global__ void k_amax_bf16(const __nv_bfloat16* __restrict__ x, size_t n, unsigned* __restrict__ out) {
     float m = 0.f;
@@ -319,7 +355,7 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
         // headroom of 8x over the calibration view's maximum: other views may see larger
         // activations, and E4M3 keeps its relative precision over a wide exponent range, so
         // the margin costs almost nothing while clipping would cost a lot
-        sc[i] = std::max(a, 1e-6f) * kFp8Headroom / 448.0f;
+        sc[i] = std::max(a, 1e-6f) * fp8_headroom() / 448.0f;
         u.convs[calls[i].layer].out_scale = sc[i];
         u.convs[calls[i].layer].out_bf16 = false;
     }
@@ -331,13 +367,12 @@ lnr_status unet_calibrate_fp8(lnr_ctx* c, Workspace& ws) {
     // BF16 operands for the first conv (the BF16 input image) and the last one (its
     // features feed the output head directly) -- optionally the whole full-resolution
     // decoder level; E4M3 everywhere else.  A producer writes BF16 for a BF16 consumer.
-    const int nenc = 2 * u.levels;
     for (size_t i = 0; i < calls.size(); ++i) {
         const ConvCall& k = calls[i];
         ConvLayer& L = u.convs[k.layer];
         L.pool_bf16 = false;
         const int p0 = producer(i, k.src0);
-        const bool bf16 = p0 < 0 || k.head_out || (kFp8Level0DecoderBf16 && k.layer >= nenc && L.level == 0);
+        const bool bf16 = p0 < 0 || k.head_out || fp8_layer_bf16(k.layer, L.level, k.layer >= 2 * u.levels);
         L.fp8 = !bf16;
         if (bf16) {
             for (const void* src : {k.src0, k.src1}) {

@@ -123,6 +123,7 @@ _VARIANTS = {
     "halo_direct_stores": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMA_STORE="0"),
     "halo_one_staging_buffer": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMA_STORE="1"),
     "halo_4_epilogue_warps": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="4"),
+    "halo_single_buffered_accumulators": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMEM1="1"),
     "halo_12_epilogue_warps": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="12"),
     "halo_12_epilogue_warps_direct_stores": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="12", LNR_CONV_TMA_STORE="0"),
 }
@@ -132,7 +133,8 @@ _VARIANTS = {
 def test_bf16_each_conv_kernel(lnr, kernel):
     """Every tensor-core conv variant (forced for every layer it applies to) meets the BF16
     bars: the generic kernel; the halo kernel with staged TMA stores (two or one buffers),
-    with direct stores, and with 4 or 12 epilogue warps."""
+    with direct stores, with 4 or 12 epilogue warps, and with tiles of twice the pixels whose
+    accumulators fill TMEM once (single-buffered)."""
     import os
     import subprocess
     import sys

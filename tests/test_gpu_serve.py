@@ -69,23 +69,37 @@ def test_served_results_equal_alone(served):
         st = r.serve_stats()
         assert st["done"] == len(reqs)
         assert st["launches"] < len(reqs) and st["max_batch"] > 1   # requests were batched
+        assert st["peak_busy_slots"] >= 2                           # batches in flight side by side
     finally:
         r.serve_stop()
 
 
 def test_admission_respects_memory_budget(served):
+    """Under a budget of 2.5 requests of the largest size (measured: the buffers one such
+    request alone makes a slot hold), batches shrink and slots release buffers so that the
+    slots together never hold more than the budget; every request still completes."""
     lnr, s, r = served
-    reqs = [q for q in _requests(s, 12, seed=4)]
+    reqs = _requests(s, 12, seed=4)
+    view = synth.random_poses(s, 1, seed=5)[0]
     r.serve_start(max_batch=4, slots=3)
     try:
-        # budget of about two requests of the largest size: batches shrink, slots wait
-        r.set_memory_budget(2 * 160 * 128 * 2200)
+        t = r.submit(view, synth.intrinsics_for(160, 128), 160, 128, 3, 1.0)
+        _wait(r, t, 160, 128)
+        one = r.serve_stats()["peak_alloc_bytes"]
+    finally:
+        r.serve_stop()
+    assert one > 0
+    budget = int(2.5 * one)
+    r.serve_start(max_batch=4, slots=3)
+    try:
+        r.set_memory_budget(budget)
         tickets = [r.submit(v, synth.intrinsics_for(W, H), W, H, nl, fs) for v, W, H, nl, fs in reqs]
         for t, (v, W, H, nl, fs) in zip(tickets, reqs):
             _wait(r, t, W, H)
         st = r.serve_stats()
         assert st["done"] == len(reqs)
-        assert st["peak_act_bytes"] <= 2 * 160 * 128 * 2200 or st["max_batch"] == 1
+        assert st["peak_alloc_bytes"] <= budget, (st, budget)
+        assert st["peak_act_bytes"] <= budget, (st, budget)
     finally:
         r.set_memory_budget(0)
         r.serve_stop()

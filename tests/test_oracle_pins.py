@@ -176,6 +176,26 @@ def _pixel_centre_point(intr, col, row, z):
     return np.array([(col + 0.5 - intr.cx) / intr.fx * z, (row + 0.5 - intr.cy) / intr.fy * z, z])
 
 
+def test_resolve_hand_case():
+    """Resolve of a hand-written key buffer (Fig. 1; Sec. 3: the image holds the colour,
+    the depth and the fill mask of each pixel's front point): a key is (float bits of z) << 32
+    | sorted position; an empty key (all ones) gives RGB 0, D = +inf, A = 0; otherwise RGB is
+    the point's colour (the scan byte of the packed colour is dropped), D = z and A = 1."""
+    def key(z, pos):
+        return (int(np.float32(z).view(np.uint32)) << 32) | pos
+    empty = (1 << 64) - 1
+    keys = np.array([[empty, key(2.5, 1), key(0.75, 0)],
+                     [empty, key(100.0, 2), key(1e-3, 1)]], np.uint64)
+    rgbs = np.array([0x07030201, 0x003264C8, 0x038000FF], np.uint32)   # (r, g, b, scan) packed
+    rgb, D, A = oracle.resolve(keys, rgbs, 3, 2)
+    assert rgb.tolist() == [[[0, 0, 0], [200, 100, 50], [1, 2, 3]],
+                            [[0, 0, 0], [255, 0, 128], [200, 100, 50]]]
+    assert A.tolist() == [[0, 1, 1], [0, 1, 1]]
+    assert np.isinf(D[0, 0]) and np.isinf(D[1, 0])
+    assert D[0, 1] == np.float32(2.5) and D[0, 2] == np.float32(0.75)
+    assert D[1, 1] == np.float32(100.0) and D[1, 2] == np.float32(1e-3)
+
+
 def test_soft_zbuffer_hand_case():
     """Soft z-buffer colours on a hand-built pixel (Sec. 3: colours of points arriving at
     similar depths are averaged): contributors are the points within z_front * (1 + rel)."""

@@ -44,3 +44,22 @@ def test_two_replicas_take_the_slowest_rank():
     assert tot0 == tot1 == 250.0
     assert fps0 == fps1 == pytest.approx(2 * 8 / 0.25)
     assert poses0 != poses1                     # ranks render different poses
+
+
+def test_bench_gpus_2_spawns_two_ranks_that_agree():
+    """`bench.py --gpus 2` run without a launcher starts two ranks itself (torchrun on
+    127.0.0.1); here with gloo ranks on the CPU: rank r reports 10 * (r + 1) ms for 8 frames
+    and rank 0 prints the job's aggregate over both ranks."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--replica-selftest"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1                       # rank 0 alone prints
+    rec = lines[0]
+    assert rec["world"] == 2 and rec["slowest_ms"] == 20.0
+    assert rec["value"] == pytest.approx(2 * 8 / 0.020)
