@@ -537,6 +537,77 @@ def run_100M(args, lnr, synth, torch, dev, B):
     return res
 
 
+def density_sweep(lnr, synth, torch, dev, scene, B, fractions=(0.1, 0.25, 0.5)):
+    """Output sensitivity (the paper's claim that cost follows the visible points, Sec. 1):
+    the multiroom_20M scan decimated to a seeded subset of its points, 8 x 1080p views per
+    step, BF16; per configuration visible points per view, raster and U-Net time (library
+    stage events) and frames/s."""
+    weights = synth.unet_weights(CH, seed=1)
+    intr = synth.intrinsics_for(W, H)
+    views = synth.random_poses(scene, N_POSES, seed=2)
+    order = np.random.default_rng(0).permutation(len(scene.xyz))
+    out = []
+    for frac in fractions:
+        keep = np.sort(order[:int(frac * len(order))])
+        r = lnr.Renderer(dev.index)
+        try:
+            r.load_cloud(scene.xyz[keep], scene.rgb[keep], scene.scan_id[keep])
+            r.build_grid(CELL)
+            r.set_unet(CH, weights, "bf16")
+            r.autotune(W, H, B)
+            vis = [r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1] for v in views[:B]]
+            fs = [FS[k % 2] for k in range(B)]
+            for _ in range(3):
+                r.render_batch(views[:B], intr, W, H, NLEV, fs)
+            r.set_timing(True)
+            tims = []
+            for i in range(5):
+                r.render_batch([views[(i + k) % len(views)] for k in range(B)], intr, W, H, NLEV, fs)
+                tims.append(r.get_timing())
+            r.set_timing(False)
+        finally:
+            r.close()
+        med = lambda k: float(np.median([t[k] for t in tims]))
+        raster = med("cull") + med("splat") + med("resolve_pyramid") + med("upsample_pack")
+        out.append({"points": int(len(keep)), "fraction": frac, "visible_points_per_view": float(np.mean(vis)),
+                    "raster_ms_per_step": raster, "splat_ms_per_step": med("splat"), "unet_ms_per_step": med("unet"),
+                    "frames_per_s": B / (med("frame") * 1e-3)})
+    return out
+
+
+def accuracy_crops(r, lnr, synth, views, weights, precisions, crop=256, margin=64):
+    """Error of each U-Net precision against the oracle's FP64 U-Net on the precision
+    workload (the 16 poses at 1920x1080): per view three aligned crops (two image corners, one
+    interior window), compared where the crop's cut edges are farther than the receptive
+    field; max abs error and the minimum over views of the PSNR of the compared pixels."""
+    import oracle
+    intr = synth.intrinsics_for(W, H)
+    fs = [FS[i % 2] for i in range(len(views))]
+    ys = {}
+    for p in precisions:
+        r.set_precision(p)
+        ys[p] = np.concatenate([r.render_batch(views[k:k + 8], intr, W, H, NLEV, fs[k:k + 8])
+                                for k in range(0, len(views), 8)])
+    res = {p: {"max_abs": 0.0, "min_psnr": 1e9, "in_unit_range": True} for p in precisions}
+    for i, v in enumerate(views):
+        x = r.render_stage(v, intr, W, H, NLEV, fs[i], lnr.STAGE_UNET_IN)
+        exp, got = [], {p: [] for p in precisions}
+        for x0, y0 in [(0, 0), (W - crop, H - crop), (832, 416)]:
+            ref = oracle.unet(np.ascontiguousarray(x[y0:y0 + crop, x0:x0 + crop]), CH, weights)
+            xa, ya = (0 if x0 == 0 else margin), (0 if y0 == 0 else margin)
+            xb, yb = (crop if x0 + crop == W else crop - margin), (crop if y0 + crop == H else crop - margin)
+            exp.append(ref[ya:yb, xa:xb].ravel())
+            for p in precisions:
+                got[p].append(ys[p][i][y0 + ya:y0 + yb, x0 + xa:x0 + xb].ravel())
+        e = np.concatenate(exp)
+        for p in precisions:
+            d = np.concatenate(got[p]).astype(np.float64) - e
+            res[p]["max_abs"] = max(res[p]["max_abs"], float(np.abs(d).max()))
+            res[p]["min_psnr"] = min(res[p]["min_psnr"], float(10 * np.log10(1.0 / max(float(np.mean(d * d)), 1e-30))))
+            res[p]["in_unit_range"] &= bool(ys[p][i].min() >= 0.0 and ys[p][i].max() <= 1.0)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,6 +617,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-100m", action="store_true", help="skip the 100M-point batched and serving legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the density sweep and the accuracy summary (FP64 oracle on crops)")
     ap.add_argument("--accuracy", type=int, default=0, metavar="VIEWS",
                     help="report max abs error and PSNR of the FP32 / BF16 / FP8 U-Nets against the "
                          "oracle's FP64 U-Net on VIEWS 1080p views (slow: the oracle runs on the host)")
@@ -728,6 +801,15 @@ def main():
             fp8 = {"unavailable": str(e)}
         r.set_precision(prec)
 
+    # ---- accuracy of every precision on the precision workload (16 views, crops) -----
+    accuracy = None
+    if have_tc and rank == 0 and not args.no_extras and fp8 and "value" in fp8:
+        accuracy = accuracy_crops(r, lnr, synth, views, weights, ("fp32", "bf16", "fp8"))
+        accuracy["views"] = len(views)
+        accuracy["compared"] = ("three 256x256 crops per view (two corners, one interior) against the oracle's "
+                                "FP64 U-Net on the bit-exact U-Net input, 64-px margins at cut edges")
+        r.set_precision(prec)
+
     # ---- served paths through the public serving API (host result buffers) --------
     from synth.requests import Request
 
@@ -769,6 +851,13 @@ def main():
         cpu = cpu_sample(oracle_grid(scene), views, weights)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     r.close()
+    sweep = None
+    if have_tc and rank == 0 and world == 1 and not args.no_extras:
+        sweep = density_sweep(lnr, synth, torch, dev, scene, B)
+        sweep.append({"points": N_POINTS, "fraction": 1.0, "visible_points_per_view": nvis_step / B,
+                      "raster_ms_per_step": stages["cull"] + stages["splat"] + stages["resolve_pyramid"] +
+                      stages["upsample_pack"], "splat_ms_per_step": stages["splat"],
+                      "unet_ms_per_step": stages["unet"], "frames_per_s": B / (stages["frame"] * 1e-3)})
     del scene
 
     big = {}
@@ -795,6 +884,8 @@ def main():
             "visible_points_per_step": nvis_step,
             "roofline_stages": roof_stages,
             "filter_cost": filter_cost,
+            "accuracy_16_views": accuracy,
+            "density_sweep": sweep,
             "grid_build_ms": grid_ms,
             "autotune_s": tune_s,
             "roofline": roof,

@@ -790,7 +790,9 @@ lnr_status lnr_calibrate_batch(lnr_ctx* c, int nviews, const lnr_view* view, con
     Workspace& ws = c->ws;
     s = prepare_views(c, ws, nviews, view, in, W, H, nlev, fs, LNR_BF16);  // the calibration frames run in BF16
     if (s != LNR_OK) return s;
+    ws.allow_fuse = false;  // the calibration reads every conv's output
     enqueue_frame(c, ws, ws.stream, -1, LNR_BF16, false);
+    ws.allow_fuse = true;
     cudaError_t e = cudaStreamSynchronize(ws.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "calibration frame");
     return unet_calibrate_fp8(c, ws);

@@ -438,9 +438,7 @@ struct HSeg {
     int wblk;        // weight blocks per chunk in memory (9, or 16 for the coarse operand)
     int bload;       // blocks staged per chunk (9; coarse: 16 for 4 classes, else the tile's y class's 8)
     int bsel;        // 1: the staged blocks start at 8 * (tile's y class)
-    int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel; or
-                     // 8 (16 bytes, the network input): tap pairs, see issue_paired
-    int paired;      // 1: 8-channel input, K = 16 per MMA covers two horizontal taps
+    int ck;          // channels per chunk (16, 32 or 64): 32, 64 or 128 bytes per pixel
     int rows;        // halo rows staged
     int nchunk;      // K chunks of this segment
     uint32_t pitch;  // bytes per staged pixel (= ck * 2)
@@ -472,6 +470,7 @@ struct HParams {
     CUtensorMap omap;    // output: 4-D {N, W, H, B} box {orow_b/e, 32, 1, 1}; parity: 5-D {N, 2, W/2, H, B}
     CUtensorMap pmap;    // pooled output: 4-D {N, W/2, H/2, B} box {prow_b/e, 16, 1, 1}
     int ostage;
+    uint32_t stg_bytes;                             // epilogue staging bytes (TMA stores)
     int ost_nbuf;                                   // staging buffers per warp (1 or 2, used in turn)
     uint32_t ost_off, ost_warp, ost_unit, ost_row, ost_pool;  // offset, bytes per warp, per buffer, row part, pool part
     uint32_t orow_b, omask, prow_b, pmask;
@@ -749,51 +748,6 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
     }
 }
 
-// The first conv, whose input has 8 channels (16 bytes per pixel, staged without swizzle):
-// a K = 16 MMA takes two horizontal taps at once.  Its A operand starts at the pixel of the
-// first tap, and the second half of K (the second 8-column core matrix) is read 16 bytes
-// on -- the next pixel -- by a leading-byte offset of 16.  Pair 0 covers taps kx = 0 and 1;
-// pair 1 starts one pixel on and covers a zero weight block and tap kx = 2.  Weight blocks
-// per pair: [first half: ky = 2, 1, 0][second half: ky = 2, 1, 0], N x 16 bytes each, so the
-// B operand's second half lies 3 blocks on.  Rows are issued as in issue_stage.
-template <int R>
-__device__ __forceinline__ void issue_paired(const IssueCtx& q, uint32_t a0, uint32_t b0, uint32_t d0, bool first) {
-    constexpr int PER = IssueSplit<R, 0>::per;
-    const uint32_t N = q.N;
-    const uint32_t row16 = kHaloW;  // one staged row of 130 pixels, in 16-byte units
-    // no swizzle: LBO (bits 16-29) and SBO (bits 32-45) in 16-byte units, version bit 46
-    const uint64_t hia = ((uint64_t)1 << 16) | ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
-    const uint64_t hib = ((uint64_t)(3 * N) << 16) | ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
-    const uint32_t d = d0 + (uint32_t)(q.g * PER) * N;
-    const uint32_t a = a0 + (uint32_t)(q.g * PER) * row16;
-    const uint32_t acc0 = first ? 0u : 1u;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const uint32_t aj = a + (uint32_t)j, bj = b0 + (uint32_t)(6 * j) * N;
-        if (j == 0) {
-#pragma unroll
-            for (int r = 0; r < PER; ++r)
-                mma_bf16(d + (uint32_t)r * N, hia | (uint64_t)(aj + (uint32_t)r * row16), hib | (uint64_t)(bj + 2 * N),
-                         q.idesc, acc0);
-#pragma unroll
-            for (int h = 1; h < PER + 2; ++h) {
-                const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h - 1 < PER - 1 ? h - 1 : PER - 1;
-                const int blk = 2 - (h - rlo);
-                mma_bf16(d + (uint32_t)rlo * N, hia | (uint64_t)(aj + (uint32_t)h * row16),
-                         hib | (uint64_t)(bj + (uint32_t)blk * N), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
-            }
-        } else {
-#pragma unroll
-            for (int h = 0; h < PER + 2; ++h) {
-                const int rlo = h - 2 > 0 ? h - 2 : 0, rhi = h < PER - 1 ? h : PER - 1;
-                const int blk = 2 - (h - rlo);
-                mma_bf16(d + (uint32_t)rlo * N, hia | (uint64_t)(aj + (uint32_t)h * row16),
-                         hib | (uint64_t)(bj + (uint32_t)blk * N), idesc_n(q.idesc, (uint32_t)(rhi - rlo + 1) * N), 1u);
-            }
-        }
-    }
-}
-
 // PAR = 0: standard tiles of R rows x 128 columns.  PAR = 1, 2 or 4: the decoder's first
 // conv; a tile is R coarse rows x 128 coarse columns and PAR of the four parity classes
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
@@ -807,7 +761,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     uint8_t* const gbase = smem_raw + (base - raw);
     const int S = p.stages;
     const uint32_t stg = base + S * p.stage_bytes;  // epilogue staging (TMA stores), 1024-aligned
-    const uint32_t bars = stg + (p.ostage ? EPI * p.ost_warp : 0u);
+    const uint32_t bars = stg + p.stg_bytes;
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (S + s); };
     auto tfull = [&](int b) { return bars + 8u * (2 * S + b); };
@@ -931,8 +885,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                     tc_fence_after();
                     const uint32_t a0 = (base + st * p.stage_bytes) >> 4;
                     const uint32_t b0 = a0 + (s.b_off >> 4);
-                    if (PAR == 0 && !IN8 && s.paired) issue_paired<R>(q, a0, b0, d0, cc == 0);
-                    else switch (nk) {
+                    switch (nk) {
                         case 1: issue_stage<R, PAR, IN8, 1>(q, sg, a0, b0, s, d0, cc == 0); break;
                         case 2: issue_stage<R, PAR, IN8, 2>(q, sg, a0, b0, s, d0, cc == 0); break;
                         default: issue_stage<R, PAR, IN8, 4>(q, sg, a0, b0, s, d0, cc == 0); break;
@@ -1275,6 +1228,260 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
     }
 }
 
+// ================================================================ fused level 0 ==
+//
+// The encoder's two full-resolution convolutions in one pass.  A tile is R output rows x
+// kFuseW output columns of the second conv.  The first conv (on the 16-channel BF16 input,
+// staged with one TMA box per tile and issued like a standard halo tile) is computed for
+// the tile and its one-pixel border: R + 2 rows x 128 columns.  Its epilogue applies bias and ReLU, rounds to BF16 and writes zero outside the
+// image (the second conv's zero padding).  It stores the result in shared memory, in the
+// swizzled K-major layout of a staged halo, so the second conv is issued on it exactly like
+// on a TMA-loaded halo (issue_stage).  The second conv's epilogue writes its output (the
+// skip tensor) and the 2x2 max-pooled output.  The first conv's output never reaches
+// global memory.  The MMA rows 126 and 127 of the second conv read border columns that are
+// never written; their results are discarded (accumulator rows are independent).
+//
+// Warps: 0 producer (both weight sets once, then one input halo per tile into an S-stage
+// ring), 1-2 MMA issuers (each takes half the rows of both convs), 3-10 the first epilogue
+// (two per TMEM lane quarter, alternate rows), 11-18 the second epilogue (two per quarter,
+// alternate row pairs).  The first conv's accumulators are single-buffered, the second
+// conv's and the shared-memory activations double-buffered.
+
+constexpr int kFuseW = 126;                 // output columns per tile
+constexpr int kFuseThreads = 32 * 19;
+constexpr int kFuseMaxN = 32;
+
+struct FParams {
+    CUtensorMap in;   // network input 4-D {16, W, H, B}, box {16, 130, R + 4, 1}, 32-byte swizzle
+    CUtensorMap w1;   // first conv: 3-D {16, N1, 9}, box {16, N1, 9}, 32-byte swizzle (blocks [kx][ky = 2, 1, 0])
+    CUtensorMap w2;   // second conv: 3-D {N1, N2, 9}, box {N1, N2, 9}, swizzled like the rows
+    int W, H, B;
+    int N1, N2;
+    int tiles_x, tiles_y, ntiles, stages;
+    uint32_t in_bytes, in_stage, w1_off, w2_off, in_off, act_off, act_bytes, w_bytes;
+    uint32_t pitch1, swz1, smask1;  // second conv's staged pixel: N1 x 2 bytes, UMMA layout, swizzle mask
+    uint32_t tmem_cols, idesc1, idesc2;
+    __nv_bfloat16* out;
+    void* pool_out;
+    int pool8;
+    float inv_pool;
+    int* err;
+    alignas(16) float b1[kFuseMaxN];
+    alignas(16) float b2[kFuseMaxN];
+};
+
+template <int R>
+__global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_constant__ FParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* const gbase = smem_raw + (base - raw);
+    const int S = p.stages;
+    const uint32_t w1s = base + p.w1_off, w2s = base + p.w2_off, ins = base + p.in_off, acts = base + p.act_off;
+    const uint32_t bars = acts + 2 * p.act_bytes;
+    auto in_full = [&](int s) { return bars + 8u * s; };
+    auto in_empty = [&](int s) { return bars + 8u * (S + s); };
+    const uint32_t wbar = bars + 8u * (2 * S);
+    const uint32_t a_full = bars + 8u * (2 * S + 1), a_empty = bars + 8u * (2 * S + 2);
+    auto act_full = [&](int b) { return bars + 8u * (2 * S + 3 + b); };
+    auto act_empty = [&](int b) { return bars + 8u * (2 * S + 5 + b); };
+    auto b_full = [&](int b) { return bars + 8u * (2 * S + 7 + b); };
+    auto b_empty = [&](int b) { return bars + 8u * (2 * S + 9 + b); };
+    const uint32_t drain = bars + 8u * (2 * S + 11);
+    const uint32_t tslot = bars + 8u * (2 * S + 12);
+    volatile int* flag = reinterpret_cast<volatile int*>(gbase + (tslot - base) + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N1 = p.N1, N2 = p.N2;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(in_full(s), 1);
+            mbar_init(in_empty(s), 2);
+        }
+        mbar_init(wbar, 1);
+        mbar_init(a_full, 2);
+        mbar_init(a_empty, 8);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(act_full(b), 1);
+            mbar_init(act_empty(b), 2);
+            mbar_init(b_full(b), 2);
+            mbar_init(b_empty(b), 8);
+        }
+        mbar_init(drain, 2);
+        flag[0] = 0;
+        flag[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (tslot - base));
+    const uint32_t accA = tmem, accB = tmem + (uint32_t)((R + 2) * N1);
+    auto tile_of = [&](int t, int& n, int& x0, int& y0) {
+        const int tx = t % p.tiles_x;
+        t /= p.tiles_x;
+        y0 = (t % p.tiles_y) * R;
+        n = t / p.tiles_y;
+        x0 = tx * kFuseW;
+    };
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ producer --
+        bool ok = true;
+        mbar_expect_tx(wbar, p.w_bytes);
+        tma_3d(w1s, &p.w1, wbar, 0, 0, 0);
+        tma_3d(w2s, &p.w2, wbar, 0, 0, 0);
+        int use = 0, st = 0;
+        uint32_t ph = 1u;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            int n, x0, y0;
+            tile_of(t, n, x0, y0);
+            if (!mbar_wait(in_empty(st), ph)) { ok = false; break; }
+            mbar_expect_tx(in_full(st), p.in_bytes);
+            tma_4d(ins + st * p.in_stage, &p.in, in_full(st), 0, x0 - 2, y0 - 2, n);
+            ++use;
+            if (++st == S) { st = 0; ph ^= 1u; }
+        }
+        if (!ok) atomicExch(p.err, 5);
+        mbar_wait(wbar, 0);
+        for (int k = use > S ? use - S : 0; k < use; ++k) mbar_wait(in_full(k % S), (k / S) & 1);
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+        // ----------------------------------------------------------------- MMA --
+        // A(k) for the k-th tile of this CTA as soon as the first epilogue has read A(k-1);
+        // then B(k-1) once its activations are in shared memory.
+        IssueCtx qa{warp - 1, 0, 0, (uint32_t)N1, p.idesc1}, qb{warp - 1, 0, 0, (uint32_t)N2, p.idesc2};
+        HSeg h1, h2;
+        h1.pitch = 32;  // the 16-channel input
+        h1.swz = 6;
+        h1.plane = 0;
+        h2.pitch = p.pitch1;
+        h2.swz = p.swz1;
+        h2.plane = 0;
+        bool ok = mbar_wait(wbar, 0);
+        int st = 0;
+        uint32_t ph = 0u;
+        for (int t = blockIdx.x, k = 0; ok; t += gridDim.x, ++k) {
+            const bool have = t < p.ntiles;
+            if (have) {
+                if (!mbar_wait(in_full(st), ph) || !mbar_wait(a_empty, (k & 1) ^ 1)) { ok = false; break; }
+                tc_fence_after();
+                issue_stage<R + 2, 0, false, 1>(qa, 0, (ins + st * p.in_stage) >> 4, w1s >> 4, h1, accA, true);
+                mma_commit(in_empty(st));
+                mma_commit(a_full);
+                if (++st == S) { st = 0; ph ^= 1u; }
+            }
+            if (k >= 1) {
+                const int kb = k - 1, ab = kb & 1;
+                if (!mbar_wait(act_full(ab), (kb >> 1) & 1) || !mbar_wait(b_empty(ab), ((kb >> 1) & 1) ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = (acts + ab * p.act_bytes) >> 4, d0 = accB + (uint32_t)(ab * R * N2);
+                if (p.pitch1 == 64) issue_stage<R, 0, false, 2>(qb, 0, a0, w2s >> 4, h2, d0, true);
+                else issue_stage<R, 0, false, 1>(qb, 0, a0, w2s >> 4, h2, d0, true);
+                mma_commit(act_empty(ab));
+                mma_commit(b_full(ab));
+            }
+            if (!have) break;
+        }
+        if (!ok) atomicExch(p.err, 6);
+        mma_commit(drain);
+        mbar_wait(drain, 0);
+    } else if (warp >= 3 && warp <= 10) {
+        // ---------------------------------------- first epilogue: activations -> smem --
+        const int q = warp & 3, m = 32 * q + lane, half = (warp - 3) >> 2;
+        const bool leader = threadIdx.x == 32 * 3;
+        for (int t = blockIdx.x, k = 0; t < p.ntiles; t += gridDim.x, ++k) {
+            const int ab = k & 1;
+            if (leader && (!mbar_wait(a_full, k & 1) || !mbar_wait(act_empty(ab), ((k >> 1) & 1) ^ 1))) flag[0] = 1;
+            named_sync(1, 256);
+            if (flag[0]) break;
+            tc_fence_after();
+            int n, x0, y0;
+            tile_of(t, n, x0, y0);
+            const int x = x0 - 1 + m;
+            const uint32_t buf = acts + ab * p.act_bytes;
+            for (int r = half; r < R + 2; r += 2) {
+                const int y = y0 - 1 + r;
+                const bool inside = x >= 0 && x < p.W && y >= 0 && y < p.H;
+                const uint32_t trow = accA + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * N1);
+                for (int c0 = 0; c0 < N1; c0 += 16) {
+                    uint32_t u[16];
+                    tmem_ld16_async(trow + (uint32_t)c0, u);
+                    tmem_wait16(u);
+                    float f[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) f[j] = inside ? fmaxf(__uint_as_float(u[j]) + p.b1[c0 + j], 0.f) : 0.f;
+                    uint4 pk[2];
+                    pack_bf16x16(f, pk);
+                    const uint32_t off = (uint32_t)(r * kHaloW + m) * p.pitch1 + (uint32_t)c0 * 2;
+                    sts_swz(buf, off, pk[0], p.smask1);
+                    sts_swz(buf, off + 16, pk[1], p.smask1);
+                }
+            }
+            tc_fence_before();
+            fence_async_smem();  // the tensor cores read these activations
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_empty);
+            named_sync(1, 256);
+            if (leader) mbar_arrive(act_full(ab));
+        }
+        if (leader && flag[0]) atomicExch(p.err, 7);
+    } else if (warp >= 11) {
+        // ------------------------------------------------ second epilogue: global stores --
+        const int q = warp & 3, m = 32 * q + lane, half = (warp - 11) >> 2;
+        const bool leader = threadIdx.x == 32 * 11;
+        const int Wh = p.W >> 1, Hh = p.H >> 1;
+        for (int t = blockIdx.x, k = 0; t < p.ntiles; t += gridDim.x, ++k) {
+            const int ab = k & 1;
+            if (leader && !mbar_wait(b_full(ab), (k >> 1) & 1)) flag[1] = 1;
+            named_sync(2, 256);
+            if (flag[1]) break;
+            tc_fence_after();
+            int n, x0, y0;
+            tile_of(t, n, x0, y0);
+            const int x = x0 + m;
+            const bool vx = m < kFuseW && x < p.W;
+            const uint32_t tb = accB + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * R * N2);
+            for (int r = 2 * half; r < R; r += 4) {
+                const int y = y0 + r;
+                for (int c0 = 0; c0 < N2; c0 += 16) {
+                    uint32_t u0[16], u1[16];
+                    tmem_ld16_async(tb + (uint32_t)(r * N2 + c0), u0);
+                    tmem_ld16_async(tb + (uint32_t)((r + 1) * N2 + c0), u1);
+                    tmem_wait16(u0);
+                    tmem_wait16(u1);
+                    float f0[16], f1[16], pm[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        f0[j] = fmaxf(__uint_as_float(u0[j]) + p.b2[c0 + j], 0.f);
+                        f1[j] = fmaxf(__uint_as_float(u1[j]) + p.b2[c0 + j], 0.f);
+                        const float a = fmaxf(f0[j], f1[j]);
+                        pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
+                    }
+                    if (vx && y < p.H) st_bf16x16(p.out + (((size_t)n * p.H + y) * p.W + x) * N2 + c0, f0);
+                    if (vx && y + 1 < p.H) st_bf16x16(p.out + (((size_t)n * p.H + y + 1) * p.W + x) * N2 + c0, f1);
+                    if (vx && (m & 1) == 0 && y + 1 < p.H) {
+                        const size_t pp = (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N2 + c0;
+                        if (p.pool8) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + pp, pm, p.inv_pool);
+                        else st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + pp, pm);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_empty(ab));
+        }
+        if (leader && flag[1]) atomicExch(p.err, 7);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
 // ------------------------------------------------------------------ host side ----
 
 // cuTensorMapEncodeTiled through the runtime's driver entry-point lookup, so that the
@@ -1304,10 +1511,7 @@ int seg_ck(int C, int ckmax) {
 }
 
 CUtensorMapSwizzle swizzle_pitch(uint32_t pitch) {
-    return pitch == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
-           : pitch == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
-           : pitch == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
-                         : CU_TENSOR_MAP_SWIZZLE_NONE;
+    return pitch == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : pitch == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
 }
 
 CUtensorMapSwizzle swizzle_for(int kc) {
@@ -1332,12 +1536,9 @@ int g_host_err = 0;  // host-side failure of a launch: 4 tensor map, 8 no FP8 co
 
 bool tc_available() { return true; }
 
-// Channels a layer's first source carries in the tensor-core layout: the RGBDA input is
-// padded to 8 (16 bytes per pixel; the halo kernel pairs taps for it, see issue_paired).
-static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 8 : L.cin0; }
-// The first conv: 8-channel input, halo kernel with tap pairs (the generic kernel needs
-// K chunks of at least 16 channels).
-static bool tc_paired(const ConvLayer& L) { return L.cin0 == 5 && !L.cin1; }
+// Channels a layer's first source carries in the tensor-core layout (the RGBDA input is
+// padded to 16 so that every K chunk is one 32-byte MMA step).
+static int tc_c0(const ConvLayer& L) { return L.cin0 == 5 ? 16 : L.cin0; }
 
 static cudaError_t prepare_halo_weights(ConvLayer& L, int ckmax);
 
@@ -1472,12 +1673,7 @@ static int ck_index(int ck) { return ck == 16 ? 0 : ck == 32 ? 1 : 2; }
 //    [cx=0 dxc=-1], 16 per chunk.
 static std::vector<uint16_t> halo_blocks(const ConvLayer& L, int sg) {
     std::vector<uint16_t> b;
-    if (tc_paired(L)) {  // [pair][half][ky = 2, 1, 0]: pair 0 = (kx 0 | kx 1), pair 1 = (zero | kx 2)
-        const int kxs[2][2] = {{0, 1}, {-1, 2}};
-        for (const auto& pr : kxs)
-            for (int kx : pr)
-                for (int ky = 2; ky >= 0; --ky) b.push_back(kx < 0 ? (uint16_t)0 : (uint16_t)(1u << (3 * ky + kx)));
-    } else if (!L.cin1) {
+    if (!L.cin1) {
         for (int j = 0; j < 9; ++j) b.push_back((uint16_t)(1u << ((2 - j % 3) * 3 + j / 3)));
     } else if (sg == 0) {
         for (int t = 0; t < 9; ++t) b.push_back((uint16_t)(1u << t));
@@ -1589,7 +1785,7 @@ cudaError_t tc_prepare_fp8(ConvLayer& L) {
 
 // Weight blocks staged per chunk: 9, or for the nearest-upsampled operand of a decoder
 // concat conv 16 (all four classes) or the 8 of the tile's y class.
-static int halo_bload(const ConvLayer& L, int kind, int P) { return tc_paired(L) ? 12 : kind == 2 ? (P == 4 ? 16 : 8) : 9; }
+static int halo_bload(int kind, int P) { return kind == 2 ? (P == 4 ? 16 : 8) : 9; }
 
 // Parity-class tiles stack the two x classes along N (MMAs of 2N columns, at most 256).
 static bool halo_parity_ok(const ConvLayer& L, int P) { return P == 1 || (P >= 2 && 2 * L.cout <= 256); }
@@ -1605,7 +1801,7 @@ static uint32_t halo_stage_bytes(const ConvLayer& L, int R, int P, int ckmax, in
         const uint32_t rows = kind1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2, pitch = (uint32_t)(esize * ck);
         const uint32_t plane = align_up(rows * kHaloW * pitch, 1024);
         const int kind = L.cin1 ? (sg == 0 ? 1 : 2) : 0;
-        const int bl = halo_bload(L, kind, P);
+        const int bl = halo_bload(kind, P);
         st = std::max(st, align_up((kind1 ? 2 : 1) * plane + (uint32_t)bl * L.cout * pitch, 1024));
     }
     return st;
@@ -1697,16 +1893,15 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         s.kind = kind;
         s.ck = seg_ck(C, ckmax);
         s.pitch = (uint32_t)s.ck * esize;
-        s.swz = s.pitch == 128 ? 2u : s.pitch == 64 ? 4u : s.pitch == 32 ? 6u : 0u;
-        s.paired = tc_paired(L) ? 1 : 0;
+        s.swz = s.pitch == 128 ? 2u : s.pitch == 64 ? 4u : 6u;
         s.rows = kind == 1 ? 2 * R + (P == 4 ? 2 : 1) : R + 2;
         s.nchunk = C / s.ck;
         const uint32_t planes = kind == 1 ? 2 : 1;
         s.plane = align_up((uint32_t)s.rows * kHaloW * s.pitch, 1024);
         s.a_bytes = planes * (uint32_t)s.rows * kHaloW * s.pitch;
         s.b_off = planes * s.plane;
-        s.wblk = s.paired ? 12 : kind == 2 ? 16 : 9;
-        s.bload = halo_bload(L, kind, P);
+        s.wblk = kind == 2 ? 16 : 9;
+        s.bload = halo_bload(kind, P);
         s.bsel = kind == 2 && P != 4;
         const uint32_t b_bytes = (uint32_t)s.bload * N * s.pitch;
         s.bytes = s.a_bytes + b_bytes;
@@ -1800,6 +1995,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
     }
+    p.stg_bytes = stg_total;
     if (stg_total + 2 * p.stage_bytes > 220u * 1024u) return false;  // staging + two pipeline stages must fit
     p.stages = std::min<int>(8, (int)((220u * 1024u - stg_total) / p.stage_bytes));
     (void)halo_stage_bytes;
@@ -1887,6 +2083,117 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
     return true;
 }
 
+// The fused level-0 encoder (k_enc0_fused): the first conv L0 on the 8-channel input and the
+// second conv L1 with its 2x2 pooled output.  R output rows per tile (2 or 4).  Returns false
+// when the pair or the types do not fit it (the caller then runs the two convs apart).
+bool tc_enc0_fused(const ConvLayer& L0, const ConvLayer& L1, const void* in, void* out, void* pool_out, int B, int W,
+                   int H, int R, cudaStream_t st, const HaloTypes& ty1) {
+    tc_init();
+    const int N1 = L0.cout, N2 = L1.cout;
+    if (L0.cin0 != 5 || L0.cin1 || L1.cin0 != N1 || L1.cin1 || !L1.pool || !pool_out || (N1 != 16 && N1 != 32) ||
+        (N2 != 16 && N2 != 32) || (R != 2 && R != 4) || ty1.in8 || ty1.out8)
+        return false;
+    const void* w1 = L0.wh[0];
+    const void* w2 = L1.wh[ck_index(N1)];
+    if (!w1 || !w2 || (int)L0.bf.size() < N1 || (int)L1.bf.size() < N2) return false;
+    FParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.W = W; p.H = H; p.B = B; p.N1 = N1; p.N2 = N2;
+    p.tiles_x = (W + kFuseW - 1) / kFuseW;
+    p.tiles_y = (H + R - 1) / R;
+    p.ntiles = B * p.tiles_x * p.tiles_y;
+    p.pitch1 = (uint32_t)N1 * 2;
+    p.swz1 = p.pitch1 == 64 ? 4u : 6u;
+    p.smask1 = p.pitch1 == 64 ? 3u : 1u;
+    p.in_bytes = (uint32_t)(R + 4) * kHaloW * 32;
+    p.in_stage = align_up(p.in_bytes, 1024);
+    const uint32_t w1b = 9u * N1 * 32, w2b = 9u * N2 * p.pitch1;
+    p.w_bytes = w1b + w2b;
+    p.w1_off = 0;
+    p.w2_off = align_up(w1b, 1024);
+    p.in_off = p.w2_off + align_up(w2b, 1024);
+    p.act_bytes = align_up((uint32_t)(R + 2) * kHaloW * p.pitch1, 1024);
+    const uint32_t budget = 220u * 1024u;
+    const uint32_t fixed = p.in_off + 2 * p.act_bytes;
+    if (fixed + 2 * p.in_stage > budget) return false;
+    p.stages = std::min<int>(4, (int)((budget - fixed) / p.in_stage));
+    p.act_off = p.in_off + (uint32_t)p.stages * p.in_stage;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)((R + 2) * N1 + 2 * R * N2)) cols <<= 1;
+    if (cols > 512) return false;
+    p.tmem_cols = cols;
+    p.idesc1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N1 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    p.idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N2 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    for (int i = 0; i < N1; ++i) p.b1[i] = L0.bf[i];
+    for (int i = 0; i < N2; ++i) p.b2[i] = L1.bf[i];
+    p.out = static_cast<__nv_bfloat16*>(out);
+    p.pool_out = pool_out;
+    p.pool8 = ty1.pool8 ? 1 : 0;
+    p.inv_pool = ty1.inv_out;
+    p.err = g_err;
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    bool ok;
+    {
+        cuuint64_t dims[4] = {16, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        cuuint64_t str[3] = {32, (cuuint64_t)W * 32, (cuuint64_t)H * W * 32};
+        cuuint32_t box[4] = {16, (cuuint32_t)kHaloW, (cuuint32_t)(R + 4), 1};
+        ok = encode_tiled(&p.in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), dims, str, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    {
+        cuuint64_t dims[3] = {16, (cuuint64_t)N1, 9};
+        cuuint64_t str[2] = {32, (cuuint64_t)N1 * 32};
+        cuuint32_t box[3] = {16, (cuuint32_t)N1, 9};
+        ok = ok && encode_tiled(&p.w1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(w1), dims, str, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)N1, (cuuint64_t)N2, 9};
+        cuuint64_t str[2] = {(cuuint64_t)p.pitch1, (cuuint64_t)N2 * p.pitch1};
+        cuuint32_t box[3] = {(cuuint32_t)N1, (cuuint32_t)N2, 9};
+        ok = ok && encode_tiled(&p.w2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(w2), dims, str, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_pitch(p.pitch1), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (!ok) {
+        g_host_err = 4;
+        return true;
+    }
+    const size_t smem = 1024 + (size_t)p.act_off + 2 * p.act_bytes + 8 * (2 * p.stages + 14) + 16;
+    const int grid = std::min(p.ntiles, g_num_sms);
+    auto launch = [&](void (*kern)(FParams)) {
+        static std::mutex mu;
+        static std::set<const void*> done;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (done.insert((const void*)kern).second)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        }
+        kern<<<grid, kFuseThreads, smem, st>>>(p);
+        if (cudaGetLastError() != cudaSuccess) g_host_err = 9;
+    };
+    if (R == 2) launch(k_enc0_fused<2>);
+    else launch(k_enc0_fused<4>);
+    return true;
+}
+
+// The fused level-0 encoder for the pair (L0, L1) at a precision: only with BF16 operands
+// for both (FP8 mode keeps them BF16 by its policy); the pooled output stores E4M3 when its
+// consumer reads E4M3.
+bool tc_fused_enc0(const ConvLayer& L0, const ConvLayer& L1, lnr_precision prec, const void* in, void* out,
+                   void* pool_out, int B, int W, int H, int R, cudaStream_t st) {
+    HaloTypes ty;
+    if (prec == LNR_FP8) {
+        if (L0.fp8 || L1.fp8) return false;
+        ty.out8 = !L1.out_bf16;
+        ty.pool8 = !L1.pool_bf16;
+        ty.inv_out = 1.0f / L1.out_scale;
+    }
+    return tc_enc0_fused(L0, L1, in, out, pool_out, B, W, H, R, st, ty);
+}
+
 void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const void* src1, void* out, void* pool_out,
              const float* head_w, const float* head_b, const float* head_wh, const float* head_bh, float* head_out, int B,
              int W, int H, int head_o, cudaStream_t st, const TcConfig* force) {
@@ -1922,7 +2229,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
     } else if (forced == 2) {
         cfg.mode = 2;
     }
-    if ((fp8 || tc_paired(L)) && cfg.mode == 2) cfg.mode = 0;  // the generic kernel: BF16, K chunks >= 16
+    if (fp8 && cfg.mode == 2) cfg.mode = 0;  // the generic kernel is BF16 only
     if (cfg.mode != 2) {
         int R = cfg.R, P = cfg.P, CK = cfg.CK;
         if (cfg.mode == 0) {
@@ -1958,7 +2265,7 @@ void tc_conv(const ConvLayer& L, lnr_precision prec, const void* src0, const voi
 std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
     std::vector<TcConfig> out;
     const bool in8 = prec == LNR_FP8 && L.fp8;
-    if (prec != LNR_FP8 && !tc_paired(L)) {
+    if (prec != LNR_FP8) {
         TcConfig g;
         g.mode = 2;
         out.push_back(g);

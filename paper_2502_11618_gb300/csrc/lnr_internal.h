@@ -42,6 +42,7 @@ struct TcConfig {
     int R = 0, P = 0, CK = 0;
     int O = 0;  // halo kernel: 1 or 2 = epilogue stores through that many staging buffers and TMA
     int E = 8;  // halo kernel: epilogue warps (4, 8, or 12 for standard tiles)
+    int F = 0;  // first conv only: 2 or 4 = fused with the second (k_enc0_fused, F output rows per tile)
 };
 
 // One convolution as the GPU runs it.
@@ -133,6 +134,7 @@ struct Workspace {
     DBuf act[4 * kMaxUnetLevels + 2];       // U-Net activations; [4 * kMaxUnetLevels] = U-Net input
     DBuf out;                               // float [B][P][3]
     float* out_ptr = nullptr;               // U-Net output of the next frame: a caller's device buffer, or null for out
+    bool allow_fuse = true;                 // false: every conv runs apart (the FP8 calibration frame reads every output)
     // View parameters go up from two pinned host blocks in turn; view_ev[k] is recorded right
     // after block k's upload, so composing the next frame waits only for the upload that
     // last used its block, never for the frame still on the device.
@@ -229,7 +231,7 @@ size_t splat_max_chunks(uint64_t npoints);  // entries per view of the splat's c
 void launch_training_input(const Workspace& ws, const float* gt, float zfar, int unfiltered, float* out,
                            cudaStream_t st);
 // Upsample step from level l+1 to level l; at l == 0 also packs the U-Net input.
-// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC8, 2 = none (stage taps only).
+// unet_in_kind: 0 = FP32 NHWC8, 1 = BF16 NHWC16, 2 = none (stage taps only).
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int unet_in_kind,
                      bool write_u0, cudaStream_t st);
 size_t pyramid_floats(int W, int H, int nlev);
@@ -256,7 +258,7 @@ lnr_status unet_prepare(lnr_ctx* c);
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
                   cudaStream_t st, cudaEvent_t* layer_ev);
 int unet_in_kind(lnr_precision p);
-size_t unet_in_bytes_per_px(lnr_precision p);  // network-input buffer bytes per pixel (the FP32 layout)
+size_t unet_in_bytes_per_px(lnr_precision p);  // network-input buffer bytes per pixel (32 in both layouts)
 
 // conv_tc.cu
 bool tc_available();
@@ -265,6 +267,9 @@ void tc_conv(const ConvLayer& L, lnr_precision p, const void* src0, const void* 
              const float* head_w, const float* head_b, const float* head_wh, const float* head_bh, float* head_out, int B,
              int W, int H, int head_o, cudaStream_t st, const TcConfig* force = nullptr);
 std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision p);
+// The first two encoder convs fused (R rows per tile, 2 or 4); false when they cannot be.
+bool tc_fused_enc0(const ConvLayer& L0, const ConvLayer& L1, lnr_precision p, const void* in, void* out,
+                   void* pool_out, int B, int W, int H, int R, cudaStream_t st);
 cudaError_t tc_prepare_fp8(ConvLayer& L);
 int tc_error_word();  // nonzero after a bounded wait in a tensor-core kernel ran out (then reset)
 

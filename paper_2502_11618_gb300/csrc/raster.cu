@@ -443,7 +443,7 @@ struct UpArgs {
     int fill;            // non-final level: fill empty pixels by interpolation
     // final level only
     const uint32_t* rgba;
-    void* unet_in;       // NHWC: 8 FP32 channels (kind 0) or 8 BF16 channels (kind 1)
+    void* unet_in;       // NHWC: 8 FP32 channels (kind 0) or 16 BF16 channels (kind 1)
     int kind;            // 0 = FP32, 1 = BF16, 2 = none
     float* u0;           // kept depth tap (nullable)
 };
@@ -456,8 +456,8 @@ __device__ __forceinline__ void st_sector(void* dst, uint32_t w0, uint32_t w1, u
                  : "memory");
 }
 
-// One pixel of the network input: 8 FP32 channels (32 bytes, one sector) or 8 BF16
-// channels (16 bytes), written with one store.
+// One pixel of the network input: 8 FP32 channels or 16 BF16 channels (32 bytes in both
+// layouts), written as one sector.
 __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, float r, float g, float b,
                                               float d, float a) {
     if (kind == 0) {
@@ -466,8 +466,8 @@ __device__ __forceinline__ void store_unet_in(void* base, int kind, size_t q, fl
     } else if (kind == 1) {
         __nv_bfloat162 v0 = __floats2bfloat162_rn(r, g), v1 = __floats2bfloat162_rn(b, d);
         __nv_bfloat162 v2 = __floats2bfloat162_rn(a, 0.f);
-        static_cast<uint4*>(base)[q] = make_uint4(*reinterpret_cast<uint32_t*>(&v0), *reinterpret_cast<uint32_t*>(&v1),
-                                                  *reinterpret_cast<uint32_t*>(&v2), 0u);
+        st_sector(static_cast<uint4*>(base) + 2 * q, *reinterpret_cast<uint32_t*>(&v0), *reinterpret_cast<uint32_t*>(&v1),
+                  *reinterpret_cast<uint32_t*>(&v2), 0u, 0u, 0u, 0u, 0u);
     }
 }
 
@@ -576,7 +576,7 @@ __global__ void k_extract5(const void* in, int kind, float* out, int64_t npx) {
     for (int c = 0; c < 5; ++c) {
         float v;
         if (kind == 0) v = static_cast<const float*>(in)[q * 8 + c];
-        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 8 + c]);
+        else v = __bfloat162float(static_cast<const __nv_bfloat16*>(in)[q * 16 + c]);
         out[q * 5 + c] = v;
     }
 }

@@ -168,9 +168,9 @@ inline int slot(int l, int k) { return 4 * l + k; }
 }  // namespace
 
 int unet_in_kind(lnr_precision p) { return p == LNR_FP32 ? 0 : 1; }
-// Bytes per pixel of the network-input buffer: the FP32 layout (8 x 4 bytes), which the stage
-// taps use at every precision; the BF16 layout (8 x 2 bytes) fits in it.
-size_t unet_in_bytes_per_px(lnr_precision) { return 8 * 4; }
+// Bytes per pixel of the network-input buffer: 8 FP32 or 16 BF16 channels (the stage taps use
+// the FP32 layout at every precision).
+size_t unet_in_bytes_per_px(lnr_precision) { return 32; }
 
 static size_t elem_bytes(lnr_precision p) { return p == LNR_FP32 ? 4 : 2; }
 
@@ -261,13 +261,40 @@ static void run_call(const Unet& u, const ConvCall& k, Workspace& ws, lnr_precis
                 u.out_ch, st, force);
 }
 
+// Rows per tile of the fused level-0 encoder for the layer resolution (W, H), or 0 to run
+// the first two convs apart: the autotuner's choice, else LNR_CONV_FUSE0=2|4 (tests).
+static int fuse_rows(const Unet& u, lnr_precision p, int W, int H) {
+    if (p == LNR_FP32 || u.convs.size() < 2) return 0;
+    static const int forced = [] {
+        const char* e = getenv("LNR_CONV_FUSE0");
+        const int v = e ? atoi(e) : 0;
+        return v == 2 || v == 4 ? v : 0;
+    }();
+    const auto& table = p == LNR_FP8 ? u.convs[0].tuned8 : u.convs[0].tuned;
+    auto it = table.find({W, H});
+    if (it != table.end() && it->second.F) return it->second.F;
+    return forced;
+}
+
 void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* in, float* out,
                   cudaStream_t st, cudaEvent_t* layer_ev) {
     const Unet& u = c->unet;
     if (unet_ensure(u, ws, p) != cudaSuccess) return;
     int ev = 0;
     if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
-    for (const ConvCall& k : unet_plan(u, ws, p, in, out)) {
+    const std::vector<ConvCall> calls = unet_plan(u, ws, p, in, out);
+    for (size_t i = 0; i < calls.size(); ++i) {
+        const ConvCall& k = calls[i];
+        if (k.layer == 0 && i + 1 < calls.size() && ws.allow_fuse) {
+            const int R = fuse_rows(u, p, k.W, k.H);
+            const ConvCall& k1 = calls[i + 1];
+            if (R && tc_fused_enc0(u.convs[0], u.convs[1], p, k.src0, k1.out, k1.pool, ws.B, k.W, k.H, R, st)) {
+                ++i;  // both convs done
+                if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
+                if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
+                continue;
+            }
+        }
         run_call(u, k, ws, p, st, nullptr);
         if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
     }
@@ -418,7 +445,10 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
         const char* v = getenv("LNR_TUNE_LOG");
         return v ? std::max(1, atoi(v)) : 0;
     }();
-    for (const ConvCall& k : unet_plan(u, ws, p, in, ws.out.as<float>())) {
+    const std::vector<ConvCall> calls = unet_plan(u, ws, p, in, ws.out.as<float>());
+    std::vector<float> best_ms(calls.size(), 0.f);
+    for (size_t ci = 0; ci < calls.size(); ++ci) {
+        const ConvCall& k = calls[ci];
         ConvLayer& L = u.convs[k.layer];
         float best = 1e30f;
         TcConfig best_cfg;
@@ -440,10 +470,35 @@ lnr_status unet_autotune(lnr_ctx* c, Workspace& ws, lnr_precision p, int reps) {
             }
         }
         if (e != cudaSuccess) break;
+        best_ms[ci] = best;
         (p == LNR_FP8 ? L.tuned8 : L.tuned)[{k.W, k.H}] = best_cfg;
         if (log)
             fprintf(stderr, "autotune layer %d %dx%d: mode %d R %d P %d ck %d O %d E %d  %.1f us\n", k.layer, k.W, k.H,
                     best_cfg.mode, best_cfg.R, best_cfg.P, best_cfg.CK, best_cfg.O, best_cfg.E, 1e3 * best / reps);
+    }
+    // the first two convs fused, against the two best separate configurations
+    if (e == cudaSuccess && calls.size() >= 2 && calls[0].layer == 0 && calls[1].layer == 1) {
+        const ConvCall &k0 = calls[0], &k1 = calls[1];
+        auto& entry = (p == LNR_FP8 ? u.convs[0].tuned8 : u.convs[0].tuned)[{k0.W, k0.H}];
+        entry.F = 0;
+        float best = best_ms[0] + best_ms[1];
+        for (int R : {2, 4}) {
+            if (!tc_fused_enc0(u.convs[0], u.convs[1], p, k0.src0, k1.out, k1.pool, ws.B, k0.W, k0.H, R, st)) continue;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r)
+                tc_fused_enc0(u.convs[0], u.convs[1], p, k0.src0, k1.out, k1.pool, ws.B, k0.W, k0.H, R, st);
+            cudaEventRecord(e1, st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (tc_error_word()) continue;
+            if (log) fprintf(stderr, "autotune fused layers 0+1 %dx%d: R %d  %.1f us (apart %.1f us)\n", k0.W, k0.H, R,
+                             1e3 * ms / reps, 1e3 * (best_ms[0] + best_ms[1]) / reps);
+            if (ms < best) {
+                best = ms;
+                entry.F = R;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

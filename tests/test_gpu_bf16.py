@@ -124,6 +124,8 @@ _VARIANTS = {
     "halo_one_staging_buffer": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMA_STORE="1"),
     "halo_4_epilogue_warps": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="4"),
     "halo_single_buffered_accumulators": dict(LNR_CONV_KERNEL="halo", LNR_CONV_TMEM1="1"),
+    "fused_level0_encoder_2_rows": dict(LNR_CONV_FUSE0="2"),
+    "fused_level0_encoder_4_rows": dict(LNR_CONV_FUSE0="4"),
     "halo_12_epilogue_warps": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="12"),
     "halo_12_epilogue_warps_direct_stores": dict(LNR_CONV_KERNEL="halo", LNR_CONV_EPI="12", LNR_CONV_TMA_STORE="0"),
 }
@@ -133,8 +135,9 @@ _VARIANTS = {
 def test_bf16_each_conv_kernel(lnr, kernel):
     """Every tensor-core conv variant (forced for every layer it applies to) meets the BF16
     bars: the generic kernel; the halo kernel with staged TMA stores (two or one buffers),
-    with direct stores, with 4 or 12 epilogue warps, and with tiles of twice the pixels whose
-    accumulators fill TMEM once (single-buffered)."""
+    with direct stores, with 4 or 12 epilogue warps, with tiles of twice the pixels whose
+    accumulators fill TMEM once (single-buffered), and the fused level-0 encoder (2 or 4
+    rows per tile)."""
     import os
     import subprocess
     import sys
@@ -164,3 +167,39 @@ def test_bf16_autotuned_kernels_meet_the_bars(lnr):
     with pytest.raises(lnr.LnrError):
         r.autotune(390, 216, 2)
     r.close()
+
+
+_FUSE_SCRIPT = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import synth
+import paper_2502_11618_gb300 as lnr
+s = synth.multiroom_scene(n_points=300_000)
+ch = (32, 64, 128, 256)
+r = lnr.Renderer(0); r.load_cloud(s.xyz, s.rgb, s.scan_id); r.build_grid(0.25)
+r.set_unet(ch, synth.unet_weights(ch, seed=3), "bf16")
+W, H = 392, 216
+views = synth.random_poses(s, 3, seed=8)
+np.save(sys.argv[1], r.render_batch(views, synth.intrinsics_for(W, H), W, H, 4, 1.0))
+"""
+
+
+def test_fused_level0_encoder_equals_the_two_convs(lnr, tmp_path):
+    """The fused level-0 encoder computes the same BF16 roundings in the same order as the
+    two convolutions run apart (one K chunk, the same tap order per row): the frames are
+    bit-identical, for 2 and 4 rows per tile, on a frame with ragged tiles."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = {}
+    for tag, extra in (("apart", {}), ("fused2", {"LNR_CONV_FUSE0": "2"}), ("fused4", {"LNR_CONV_FUSE0": "4"})):
+        env = {k: v for k, v in os.environ.items() if not k.startswith("LNR_CONV")}
+        env.update(extra)
+        path = str(tmp_path / f"{tag}.npy")
+        r = subprocess.run([sys.executable, "-c", _FUSE_SCRIPT.format(root=root), path], env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        outs[tag] = np.load(path)
+    assert np.array_equal(outs["fused2"], outs["apart"])
+    assert np.array_equal(outs["fused4"], outs["apart"])
