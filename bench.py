@@ -131,13 +131,14 @@ def peaks():
 
 
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
-# (8 x 1080p views, BF16), from one ncu capture of the conv kernels.  It describes the conv
-# kernels as captured: reported only while their sources are unchanged.
-CONV_TRAFFIC = {"bytes_per_step": 14272.9e6,
+# (8 x 1080p views, BF16): ncu DRAM counters of the twelve separate conv launches at 2 views
+# (x 4) and of the fused level-0 encoder at 1 view (x 8), scaled by the views processed.  It
+# describes the conv kernels as captured: reported only while their sources are unchanged.
+CONV_TRAFFIC = {"bytes_per_step": 10317.9e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "5fc8698b096b8d115707aa700c31931e89f5f528fb5d9d96c379bbadd45756e6",
+                           "11b2ad7b144da040c988280b3828f38f41a7449bc72a912e41af53c60451fcd6",
                            "paper_2502_11618_gb300/csrc/unet.cu":
-                           "83a0159cfb46a21621283777895b1b70de98e4ca132ce2a83de4e2c62d5aa23c"}}
+                           "50b2e4b682991f0ce99dbc367162030fad168bac7175a93ff244f18119f9eecc"}}
 
 
 def conv_traffic():
@@ -399,18 +400,23 @@ def percentiles(lat_ms):
 _PINNED = {}   # (W, H) -> free page-locked result buffers, reused across serving runs
 
 
-def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, window=48):
+def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, window=48, session=True):
     """Serve `reqs` (synth.requests.Request) through lnr_submit_into / lnr_poll: at their
     arrival times when realtime, else closed loop with at most `window` requests
     outstanding.  Every result is copied by the device straight into a page-locked host
     buffer of the caller (a pool per resolution, reused once a result has been polled).
-    Returns (frames/s, latencies in ms, serving stats)."""
+    session=False: serving is already started (and stays started).  Returns (frames/s,
+    latencies in ms, serving stats -- cumulative over the serving session)."""
     import torch
-    r.set_precision(precision)
+    if session:
+        r.set_precision(precision)
     pools = _PINNED
-    for key in {(q.W, q.H) for q in reqs}:    # page-locked buffers exist before the clock starts
+    # page-locked buffers exist before the clock starts: `window` per resolution in a closed
+    # loop; under arrivals, enough for the requests that can be outstanding near saturation
+    cap = window if not realtime else 2 * window
+    for key in {(q.W, q.H) for q in reqs}:
         free = pools.setdefault(key, [])
-        need = min(window, sum(1 for q in reqs if (q.W, q.H) == key))
+        need = min(cap, sum(1 for q in reqs if (q.W, q.H) == key))
         while len(free) < need:
             free.append(torch.empty((key[1], key[0], 3), dtype=torch.float32, pin_memory=True))
     lat, pending = [], []
@@ -419,7 +425,8 @@ def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, win
         free = pools[(w_, h_)]
         return free.pop() if free else torch.empty((h_, w_, 3), dtype=torch.float32, pin_memory=True)
 
-    r.serve_start(max_batch=max_batch, slots=slots)
+    if session:
+        r.serve_start(max_batch=max_batch, slots=slots)
     try:
         t0 = time.perf_counter()
         i, n = 0, len(reqs)
@@ -431,19 +438,22 @@ def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, win
                 pending.append((r.submit_into(q.view, synth.intrinsics_for(q.W, q.H), q.W, q.H, q.n_levels, q.fs, b),
                                 b, (q.W, q.H)))
                 i += 1
-            still = []
+            # results complete roughly in submission order: poll the oldest ones until one is
+            # still in flight
+            done = 0
             for tk, b, key in pending:
                 res, l = r.poll(tk)
                 if l is None:
-                    still.append((tk, b, key))
-                else:
-                    lat.append(1e3 * l)
-                    pools[key].append(b)
-            pending = still
+                    break
+                lat.append(1e3 * l)
+                pools[key].append(b)
+                done += 1
+            pending = pending[done:]
         span = time.perf_counter() - t0
         st = r.serve_stats()
     finally:
-        r.serve_stop()
+        if session:
+            r.serve_stop()
     return n / span, lat, st
 
 
@@ -498,36 +508,42 @@ def run_100M(args, lnr, synth, torch, dev, B):
                                "grid_build_ms": grid_ms, "scene_generation_s": gen_s}
         del out
         # ---- mixed-resolution serving ------------------------------------------------
-        n_bf16 = 2000
-        warm = request_stream(scene, 96, None, seed=7)
-        serve_stream(r, lnr, synth, warm, "bf16", B, 3, False)          # graphs, pinned buffers
-        bf16_fps, bf16_lat, st = serve_stream(r, lnr, synth, request_stream(scene, n_bf16, None,
-                                                                              seed=3), "bf16", B, 3, False)
+        # plain FP32 per request (one request per launch, one slot), closed loop then Poisson
         n_fp32 = max(60, 6 * args.steps)
+        warm = request_stream(scene, 96, None, seed=7)
         serve_stream(r, lnr, synth, warm[:6], "fp32", 1, 1, False)
-        fp32_fps, _, _ = serve_stream(r, lnr, synth, request_stream(scene, n_fp32, None, seed=3),
-                                      "fp32", 1, 1, False)
+        fp32_fps, _, _ = serve_stream(r, lnr, synth, request_stream(scene, n_fp32, None, seed=3), "fp32", 1, 1, False)
         lam = 0.7 * fp32_fps
         n_open = max(60, int(4 * lam))
         open_reqs = request_stream(scene, n_open, lam, seed=3)
-        _, b_lat, _ = serve_stream(r, lnr, synth, open_reqs, "bf16", B, 3, True)
         _, f_lat, _ = serve_stream(r, lnr, synth, open_reqs, "fp32", 1, 1, True)
-        sweep = []
-        for mult in (0.25, 0.5, 0.75, 0.9, 1.0, 1.25):
-            lam_k = mult * bf16_fps
-            n_k = 600
-            fps_k, lat_k, st_k = serve_stream(r, lnr, synth, request_stream(scene, n_k, lam_k,
-                                                                            seed=30 + int(100 * mult)),
-                                              "bf16", B, 3, True)
-            sweep.append({"arrivals_per_s": lam_k, "of_closed_loop": mult, "requests": n_k,
-                          "frames_per_s": fps_k, **percentiles(lat_k), "max_batch_seen": st_k["max_batch"],
-                          "peak_slots_busy": st_k.get("peak_busy_slots")})
+        # BF16 in one serving session: warm-up, closed loop, the same Poisson stream, then the
+        # arrival rate stepped up to saturation
+        n_bf16 = 2000
+        r.set_precision("bf16")
+        r.serve_start(max_batch=B, slots=3)
+        try:
+            serve_stream(r, lnr, synth, request_stream(scene, 400, None, seed=7), "bf16", B, 3, False, session=False)
+            bf16_fps, bf16_lat, st = serve_stream(r, lnr, synth, request_stream(scene, n_bf16, None, seed=3), "bf16",
+                                                  B, 3, False, session=False)
+            _, b_lat, _ = serve_stream(r, lnr, synth, open_reqs, "bf16", B, 3, True, session=False)
+            sweep = []
+            for mult in (0.25, 0.5, 0.75, 0.9, 1.0, 1.25):
+                lam_k = mult * bf16_fps
+                n_k = 600
+                fps_k, lat_k, _ = serve_stream(r, lnr, synth, request_stream(scene, n_k, lam_k, seed=30 + int(100 * mult)),
+                                               "bf16", B, 3, True, session=False)
+                sweep.append({"arrivals_per_s": lam_k, "of_closed_loop": mult, "requests": n_k,
+                              "frames_per_s": fps_k, **percentiles(lat_k)})
+            st = r.serve_stats()
+        finally:
+            r.serve_stop()
         res["served_mix"] = {
             "workload": "multiroom_100M resident; requests uniform over 1280x720 / 1920x1080 / 2560x1440, "
                         "n_levels uniform in 4..6, filter_strength U[0.5, 1.5], seeded poses",
             "served_bf16": {"value": bf16_fps, "unit": "frames/s", "requests": n_bf16, "closed_loop": True,
                             "max_batch": B, "slots": 3, **percentiles(bf16_lat),
-                            "peak_slots_busy": st.get("peak_busy_slots")},
+                            "session_max_batch": st.get("max_batch"), "session_peak_slots_busy": st.get("peak_busy_slots")},
             "plain_fp32": {"value": fp32_fps, "unit": "frames/s", "requests": n_fp32, "closed_loop": True},
             "poisson": {"arrivals_per_s": lam, "requests": n_open, "rule": "0.7 x plain FP32 closed-loop rate",
                         "served_bf16": percentiles(b_lat), "plain_fp32": percentiles(f_lat)},
@@ -767,7 +783,8 @@ def main():
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = conv_traffic() if have_tc else None
-    roof["traffic_scope"] = "DRAM bytes read + written by all U-Net conv launches of one step (ncu)"
+    roof["traffic_scope"] = ("DRAM bytes read + written by all U-Net conv launches of one step (ncu at 2 views and, "
+                             "for the fused level-0 encoder, 1 view; scaled by the views processed)")
     roof_stages = stage_roofline(stages, nvis_step, W * H * B, hbm)
     filter_cost = {"n_levels": [0, NLEV],
                    "filter_ms_per_step": [stages0["upsample_pack"], stages["upsample_pack"]],
@@ -829,9 +846,9 @@ def main():
     lam = 0.7 * plain_fps                      # both paths stable at this arrival rate
     n_open = max(40, int(3 * lam))             # about 3 s of arrivals
     prec_fast = "bf16" if have_tc else "fp32"
-    # closed loop: 320 requests, 48 outstanding at a time (about 0.2 s of work), median of
+    # closed loop: 640 requests, 48 outstanding at a time (about 0.4 s of work), median of
     # three runs
-    srv = [serve_run(prec_fast, 8, 3, 8 * max(40, args.steps), None, 11 + k) for k in range(3)]
+    srv = [serve_run(prec_fast, 8, 3, 16 * max(40, args.steps), None, 11 + k) for k in range(3)]
     srv_runs = [x[0] for x in srv]
     srv_fps = float(np.median(srv_runs))
     _, srv_lat, _ = serve_run(prec_fast, 8, 3, n_open, lam, 12)
@@ -843,7 +860,7 @@ def main():
            "path": "serving API (lnr_submit_into / lnr_poll), BF16, closed loop with 48 requests outstanding, "
                    "results copied by the device into page-locked host buffers of the caller",
            "h2d_bytes_per_step": 96 + 24 + 4, "d2h_bytes_per_step": W * H * 3 * 4, "step": "one request",
-           "runs": [round(float(x), 1) for x in srv_runs], "requests_per_run": 8 * max(40, args.steps),
+           "runs": [round(float(x), 1) for x in srv_runs], "requests_per_run": 16 * max(40, args.steps),
            "peak_slots_busy": max(x[2].get("peak_busy_slots") or 0 for x in srv)}
 
     cpu = None

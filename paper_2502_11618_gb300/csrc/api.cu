@@ -42,7 +42,7 @@ void Workspace::release() {
         if (e) { cudaEventDestroy(e); e = nullptr; }
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
-    graph_warm.clear();
+    graph_uses.clear();
 }
 
 size_t Workspace::device_bytes() const {
@@ -258,7 +258,7 @@ size_t frame_bytes(const lnr_ctx* c, int B, int W, int H, bool soft) {
 }
 
 // Enqueue a whole frame batch on ws.stream: replayed from a CUDA graph captured for this
-// (batch, size, levels, precision) once the configuration has run eagerly once; graphs are
+// (batch, size, levels, precision) once the configuration has run eagerly twice; graphs are
 // dropped whenever a buffer they captured was reallocated or the cloud / net changed.
 cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph) {
     if (!use_graph) {
@@ -271,15 +271,19 @@ cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_gr
         ws.graphs.size() >= 32) {
         for (auto& kv : ws.graphs) cudaGraphExecDestroy(kv.second);
         ws.graphs.clear();
-        ws.graph_warm.clear();
+        ws.graph_uses.clear();
         ws.graph_gen = ws.alloc_gen;
         ws.graph_cloud = c->cloud_gen;
         ws.graph_unet = c->unet_gen;
     }
     auto it = ws.graphs.find(key);
     if (it == ws.graphs.end()) {
-        if (!ws.graph_warm.count(key) || ws.keys_dirty) {  // first run of this configuration: eager
-            ws.graph_warm.insert(key);
+        // The first two runs of a configuration are eager: capturing costs more than an eager
+        // run, so a configuration is captured only once it recurs (a served stream of mixed
+        // resolutions, depths and batch sizes meets many configurations only once or twice).
+        int& uses = ws.graph_uses[key];
+        if (uses < 2 || ws.keys_dirty) {
+            ++uses;
             enqueue_frame(c, ws, ws.stream, -1, prec, false);
             return cudaGetLastError();
         }

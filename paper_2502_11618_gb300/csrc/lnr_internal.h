@@ -147,7 +147,7 @@ struct Workspace {
     // CUDA graphs of whole frames, per (B, W, H, nlev, precision); valid while no buffer
     // they captured has been reallocated (alloc_gen) and the cloud / net are unchanged
     std::map<GraphKey, cudaGraphExec_t> graphs;
-    std::set<GraphKey> graph_warm;
+    std::map<GraphKey, int> graph_uses;     // eager runs of a configuration not captured yet
     uint64_t alloc_gen = 0, graph_gen = 0, graph_cloud = 0, graph_unet = 0;
     void release();
     size_t device_bytes() const;            // device memory held by the buffers above
