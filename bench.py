@@ -406,28 +406,36 @@ def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, win
     outstanding.  Every result is copied by the device straight into a page-locked host
     buffer of the caller (a pool per resolution, reused once a result has been polled).
     session=False: serving is already started (and stays started).  Returns (frames/s,
-    latencies in ms, serving stats -- cumulative over the serving session)."""
+    latencies in ms, serving stats of this run: requests, launches, mean batch, and the
+    result buffers that had to be allocated inside the timed region)."""
     import torch
     if session:
         r.set_precision(precision)
     pools = _PINNED
-    # page-locked buffers exist before the clock starts: `window` per resolution in a closed
-    # loop; under arrivals, enough for the requests that can be outstanding near saturation
-    cap = window if not realtime else 2 * window
+    # page-locked buffers exist before the clock starts (pinning memory inside the timed
+    # region would stall the client for milliseconds per buffer): `window` per resolution in
+    # a closed loop; under arrivals, one per request, since past saturation every request
+    # can be outstanding at once
     for key in {(q.W, q.H) for q in reqs}:
         free = pools.setdefault(key, [])
-        need = min(cap, sum(1 for q in reqs if (q.W, q.H) == key))
+        count = sum(1 for q in reqs if (q.W, q.H) == key)
+        need = count if realtime else min(window, count)
         while len(free) < need:
             free.append(torch.empty((key[1], key[0], 3), dtype=torch.float32, pin_memory=True))
     lat, pending = [], []
+    allocs = [0]
 
     def buf(w_, h_):
         free = pools[(w_, h_)]
-        return free.pop() if free else torch.empty((h_, w_, 3), dtype=torch.float32, pin_memory=True)
+        if free:
+            return free.pop()
+        allocs[0] += 1
+        return torch.empty((h_, w_, 3), dtype=torch.float32, pin_memory=True)
 
     if session:
         r.serve_start(max_batch=max_batch, slots=slots)
     try:
+        st0 = r.serve_stats()
         t0 = time.perf_counter()
         i, n = 0, len(reqs)
         while i < n or pending:
@@ -451,6 +459,9 @@ def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, win
             pending = pending[done:]
         span = time.perf_counter() - t0
         st = r.serve_stats()
+        nl = st["launches"] - st0["launches"]
+        st = {**st, "run_requests": n, "run_launches": nl, "run_mean_batch": n / max(nl, 1),
+              "run_buffer_allocs": allocs[0]}
     finally:
         if session:
             r.serve_stop()
@@ -531,10 +542,12 @@ def run_100M(args, lnr, synth, torch, dev, B):
             for mult in (0.25, 0.5, 0.75, 0.9, 1.0, 1.25):
                 lam_k = mult * bf16_fps
                 n_k = 600
-                fps_k, lat_k, _ = serve_stream(r, lnr, synth, request_stream(scene, n_k, lam_k, seed=30 + int(100 * mult)),
-                                               "bf16", B, 3, True, session=False)
+                fps_k, lat_k, st_k = serve_stream(r, lnr, synth, request_stream(scene, n_k, lam_k,
+                                                                                seed=30 + int(100 * mult)),
+                                                  "bf16", B, 3, True, session=False)
                 sweep.append({"arrivals_per_s": lam_k, "of_closed_loop": mult, "requests": n_k,
-                              "frames_per_s": fps_k, **percentiles(lat_k)})
+                              "frames_per_s": fps_k, **percentiles(lat_k), "mean_batch": st_k["run_mean_batch"],
+                              "buffer_allocs_timed": st_k["run_buffer_allocs"]})
             st = r.serve_stats()
         finally:
             r.serve_stop()
@@ -747,25 +760,24 @@ def main():
         return
 
     # ---- stage timing of the batched path (library stage events on its stream) -------
-    vis = [r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1] for v in views]
-
     def stage_times(nlev, n=3):
+        """Median stage times of n timed steps, their mean visible points and the kernels
+        one step launches (the library's own counts)."""
         nlev_run[0] = nlev
         r.set_timing(True)
-        tims, nv = [], []
+        tims = []
         for i in range(n):
             step(i)
             torch.cuda.synchronize()
             tims.append(r.get_timing())
-            nv.append(sum(vis[pose_idx(i * B + k)] for k in range(B)))
         r.set_timing(False)
         nlev_run[0] = NLEV
         med = {k: float(np.median([t[k] for t in tims]))
                for k in ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame"]}
-        return med, float(np.mean(nv))
+        return med, float(np.mean([t["visible_points"] for t in tims])), int(max(t["kernels"] for t in tims))
 
-    stages, nvis_step = stage_times(NLEV)
-    stages0, _ = stage_times(0)
+    stages, nvis_step, launches_per_step = stage_times(NLEV)
+    stages0, _, _ = stage_times(0)
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6784.5)
     unet_ms = stages["unet"]
@@ -881,7 +893,6 @@ def main():
     if have_tc and not args.no_100m and world == 1:
         big = run_100M(args, lnr, synth, torch, dev, B)
 
-    launches_per_step = 3 + 1 + 1 + NLEV + 2 * (2 * len(CH) - 1) + (0 if have_tc else 1)  # cull, splat, resolve, upsample, convs
     if rank == 0:
         cfg = dict(CONFIG)
         cfg.update({"views_per_step": B, "precision": prec, "parallelism": f"replicas{world}",

@@ -191,8 +191,8 @@ lnr_status lnr_render_stage(lnr_ctx* ctx, const lnr_view* view, const lnr_intrin
 /* Render nviews views of one resolution in one pass: every view's splat, filter and
  * U-Net run batched (the U-Net on an NHWC batch).  views, intr and fs are arrays of
  * nviews; out_rgb holds nviews*H*W*3 floats, view-major.  With out_on_device the U-Net
- * writes out_rgb directly (the frame's CUDA graph is kept per output buffer, for up to 32
- * buffers).  One resolution and pyramid depth per call: views of other sizes go to other
+ * writes out_rgb directly (the frame's CUDA graph is kept per configuration and output
+ * buffer, for up to 256 of them).  One resolution and pyramid depth per call: views of other sizes go to other
  * calls, or to the serving loop, which runs batches of different sizes side by side on
  * its slots.  Same errors as lnr_render. */
 lnr_status lnr_render_batch(lnr_ctx* ctx, int nviews, const lnr_view* views,
@@ -268,11 +268,12 @@ lnr_status lnr_serve_stats(lnr_ctx* ctx, uint64_t out[6]);
 
 /* ---- measurement ------------------------------------------------------------------- */
 
-/* Device time (ms) of each stage of the most recent lnr_render / lnr_render_batch with
- * timing enabled: out[0] cull, out[1] splat, out[2] resolve+pyramid, out[3] upsample and
- * pack, out[4] U-Net, out[5] whole frame; out[6] the dominant conv layer's time, out[7] the
- * number of kernels launched.  Timing adds CUDA events to the stream; enable = 0 removes
- * them. */
+/* Measurements of the most recent lnr_render / lnr_render_batch with timing enabled.
+ * Device time (ms) of each stage: out[0] cull, out[1] splat, out[2] resolve+pyramid,
+ * out[3] upsample and pack, out[4] U-Net, out[5] whole frame.  out[6] the visible points
+ * of the batch (the cull's totals, summed over the views); out[7] the number of kernels
+ * the frame launched.  With timing on, frames run eagerly (not from a captured graph) and
+ * the call waits for the device; enable = 0 turns it off. */
 lnr_status lnr_set_timing(lnr_ctx* ctx, int enable);
 lnr_status lnr_get_timing(lnr_ctx* ctx, double out[8]);
 

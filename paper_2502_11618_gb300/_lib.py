@@ -365,5 +365,5 @@ class Renderer:
     def get_timing(self):
         o = np.zeros(8, np.float64)
         self._check(self._L.lnr_get_timing(self._c, _ptr(o)))
-        keys = ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame", "top_conv", "kernels"]
+        keys = ["cull", "splat", "resolve_pyramid", "upsample_pack", "unet", "frame", "visible_points", "kernels"]
         return dict(zip(keys, o.tolist()))

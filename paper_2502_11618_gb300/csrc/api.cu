@@ -260,15 +260,18 @@ size_t frame_bytes(const lnr_ctx* c, int B, int W, int H, bool soft) {
 // Enqueue a whole frame batch on ws.stream: replayed from a CUDA graph captured for this
 // (batch, size, levels, precision) once the configuration has run eagerly twice; graphs are
 // dropped whenever a buffer they captured was reallocated or the cloud / net changed.
+constexpr size_t kMaxGraphs = 256;
+
 cudaError_t run_frame(lnr_ctx* c, Workspace& ws, lnr_precision prec, bool use_graph) {
     if (!use_graph) {
         enqueue_frame(c, ws, ws.stream, -1, prec, false);
         return cudaGetLastError();
     }
     const GraphKey key{ws.B, ws.W, ws.H, ws.nlev, (int)prec, ws.vk, ws.out_ptr};
-    // graphs for many different caller buffers are not kept: start over past 32
+    // at most kMaxGraphs configurations are kept (a served mix of 3 resolutions x 3 depths x
+    // 8 batch sizes x 2 view blocks has 144); past that, start over
     if (ws.graph_gen != ws.alloc_gen || ws.graph_cloud != c->cloud_gen || ws.graph_unet != c->unet_gen ||
-        ws.graphs.size() >= 32) {
+        ws.graphs.size() >= kMaxGraphs) {
         for (auto& kv : ws.graphs) cudaGraphExecDestroy(kv.second);
         ws.graphs.clear();
         ws.graph_uses.clear();
@@ -314,6 +317,12 @@ static void read_timing(lnr_ctx* c, Workspace& ws) {
     }
     cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[5]);
     c->times[5] = ms;
+    // visible points of the batch: the cull's per-view totals {cells, points}
+    std::vector<uint32_t> tot(2 * (size_t)ws.B);
+    double nvis = 0.0;
+    if (cudaMemcpy(tot.data(), ws.vis_tot.p, 8 * (size_t)ws.B, cudaMemcpyDeviceToHost) == cudaSuccess)
+        for (int v = 0; v < ws.B; ++v) nvis += tot[2 * v + 1];
+    c->times[6] = nvis;
 }
 
 static lnr_status finish_output(lnr_ctx* c, Workspace& ws, float* out, size_t nfloat, int on_device) {
@@ -673,8 +682,11 @@ lnr_status lnr_render_batch(lnr_ctx* c, int nviews, const lnr_view* views, const
     s = prepare_views(c, ws, nviews, views, in, W, H, nlev, fs, c->prec);
     if (s != LNR_OK) return s;
     if (on_device) ws.out_ptr = out;  // the U-Net head writes the caller's buffer
-    if (c->timing) enqueue_frame(c, ws, ws.stream, -1, c->prec, true);
-    else {
+    if (c->timing) {
+        const uint64_t k0 = tl_launches;
+        enqueue_frame(c, ws, ws.stream, -1, c->prec, true);
+        c->times[7] = (double)(tl_launches - k0);
+    } else {
         cudaError_t e = run_frame(c, ws, c->prec, true);
         if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
     }

@@ -1653,6 +1653,7 @@ static void tc_conv_generic(const ConvLayer& L, const void* src0, const void* sr
     const int grid = std::min(p.ntiles, g_num_sms);
     if (g_host_err || !L.wtc) return;
     k_conv_tc<<<grid, kThreads, smem, st>>>(p);
+    count_launch();
 }
 
 // ---- halo kernel host side ----
@@ -2047,6 +2048,7 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
         kern<<<grid, threads, smem, st>>>(p);
+        count_launch();
         if (cudaGetLastError() != cudaSuccess) g_host_err = 9;  // a launch that did not start: reported, never silent
     };
     auto pick4 = [&](auto par, auto ep) {
@@ -2172,6 +2174,7 @@ bool tc_enc0_fused(const ConvLayer& L0, const ConvLayer& L1, const void* in, voi
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         }
         kern<<<grid, kFuseThreads, smem, st>>>(p);
+        count_launch();
         if (cudaGetLastError() != cudaSuccess) g_host_err = 9;
     };
     if (R == 2) launch(k_enc0_fused<2>);

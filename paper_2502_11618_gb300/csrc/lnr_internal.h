@@ -24,6 +24,11 @@ constexpr int kMaxLevels = 6;      // filter pyramid depth handled by the 64x64 
 constexpr int kPyrTile = 64;       // resolve + min-pool tile side
 constexpr int kMaxUnetLevels = 8;
 
+// Kernels launched by the calling thread: every launch site of the frame path adds one, so
+// that a frame's launch count is the difference across its enqueue.
+inline thread_local uint64_t tl_launches = 0;
+inline void count_launch() { ++tl_launches; }
+
 // Parameters of one view on the device (filled by the host in FP64, then rounded once).
 struct ViewDev {
     int32_t anchor[3];

@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(kSplatThreads, 4) k_splat(
         reinterpret_cast<uint32_t*>(sv)[i] = reinterpret_cast<const uint32_t*>(views)[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint32_t below = (1u << lane) - 1u;  // lanes before this one
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const float Wf = (float)W, Hf = (float)H;
@@ -594,12 +593,15 @@ void launch_cull(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                               c->dims[1], c->dims[2], c->ncells, ws.W, ws.H,
                                               ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
                                               ws.cull_bsum.as<uint32_t>(), nb);
+    count_launch();
     k_cull_scan<<<ws.B, kCullThreads, 0, st>>>(ws.cull_bsum.as<uint32_t>(), nb, ws.vis_tot.as<uint32_t>());
+    count_launch();
     dim3 g3((unsigned)((c->ncells + 255) / 256), ws.B);
     k_cull_compact<<<g3, 256, 0, st>>>(ws.view.as<ViewDev>(), ws.cull_flag.as<uint32_t>(), ws.cull_cnt.as<uint32_t>(),
                                        ws.cull_bsum.as<uint32_t>(), nb, c->ncells, c->dims[0], c->dims[1],
                                        c->cell_start.as<uint32_t>(), ws.vis_info.as<float4>(), ws.vis_pref.as<uint32_t>(),
                                        ws.chunk_cell.as<uint32_t>(), splat_max_chunks(c->n));
+    count_launch();
 }
 
 // Grid of the splat: as many blocks as fit on the GPU at once (the warps stride through the
@@ -627,6 +629,7 @@ static void splat_views(const lnr_ctx* c, Workspace& ws, cudaStream_t st, float 
             ws.keys.as<unsigned long long>() + v0 * P, SOFT ? c->rgbs.as<uint32_t>() : nullptr,
             SOFT ? ws.soft_acc.as<unsigned long long>() + 2 * v0 * P : nullptr, scale,
             ws.chunk_cell.as<uint32_t>() + (size_t)v0 * mc, mc, SOFT ? 0u : c->shard_base);
+        count_launch();
     }
 }
 
@@ -698,6 +701,7 @@ void launch_clear_keys(Workspace& ws, cudaStream_t st) {
     // earlier, larger frame behind
     size_t n = ws.keys.bytes / 8;
     k_fill_u64<<<1024, 256, 0, st>>>(ws.keys.as<unsigned long long>(), n);
+    count_launch();
     ws.keys_dirty = false;
 }
 
@@ -719,6 +723,7 @@ void launch_resolve_pyramid(const lnr_ctx* c, Workspace& ws, cudaStream_t st) {
                                          pyramid_floats(ws.W, ws.H, ws.nlev),
                                          c->soft_rel > 0.0f ? ws.soft_acc.as<unsigned long long>() : nullptr, c->shard_base,
                                          (uint32_t)c->n);
+    count_launch();
 }
 
 void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int kind, bool write_u0,
@@ -740,6 +745,7 @@ void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int 
         a.Mf = ws.depth.as<float>();
         a.f_stride = P;
         k_pack_direct<<<2048, 256, 0, st>>>(a, ws.B);
+        count_launch();
         return;
     }
     if (l == 0) { a.Mf = ws.depth.as<float>(); a.f_stride = P; }
@@ -751,6 +757,7 @@ void launch_upsample(const lnr_ctx* c, Workspace& ws, int l, void* unet_in, int 
     if (l > 0) { a.Uf = ws.pyr_u.as<float>() + pyramid_offset(ws.W, ws.H, l); a.uf_stride = pstride; a.fill = 1; }
     dim3 g((a.Wc + 31) / 32, (a.Hc + 7) / 8, ws.B);
     k_upsample<<<g, 256, 0, st>>>(a);
+    count_launch();
 }
 
 // Network input of one synthetic training pair (Sec. 3, "Training Data Generation"): per pixel from the

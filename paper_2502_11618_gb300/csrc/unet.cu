@@ -153,12 +153,15 @@ void conv_f32(const ConvLayer& L, const float* src0, const float* src1, float* o
     if (L.cout % 64 == 0) {
         dim3 g((W + 63) / 64, (H + 1) / 2, B * (L.cout / 64));
         k_conv3x3_f32<64, 64><<<g, 256, 0, st>>>(a);
+        count_launch();
     } else if (L.cout % 32 == 0) {
         dim3 g((W + 127) / 128, (H + 1) / 2, B * (L.cout / 32));
         k_conv3x3_f32<128, 32><<<g, 256, 0, st>>>(a);
+        count_launch();
     } else {
         dim3 g((W + 255) / 256, (H + 1) / 2, B * (L.cout / 16));
         k_conv3x3_f32<256, 16><<<g, 256, 0, st>>>(a);
+        count_launch();
     }
 }
 
@@ -303,6 +306,7 @@ void unet_forward(const lnr_ctx* c, Workspace& ws, lnr_precision p, const void* 
         size_t npx = (size_t)ws.B * ws.W * ws.H;
         k_head_f32<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>((const float*)deep, u.ch[0], u.head_w, u.head_b,
                                                                   u.out_ch, out, npx);
+        count_launch();
         if (layer_ev) cudaEventRecord(layer_ev[ev++], st);
     }
 }

@@ -111,6 +111,36 @@ def test_batch_equals_single(lnr, room, room_renderer):
         assert np.array_equal(yb[i], y1)
 
 
+def test_timing_reports_visible_points_and_launches(lnr, room, room_renderer):
+    """lnr_get_timing after a timed batch: stage times that add up to the frame's, the
+    batch's visible points (the oracle's splat count summed over the views) and the frame's
+    kernel launches -- cull 3, splat 1, resolve 1, one upsample per pyramid level, then the
+    FP32 U-Net's 2 (2L - 1) convs and its head for L = 3 levels."""
+    s, g = room
+    W, H, nl = 128, 96, 3
+    intr = synth.intrinsics_for(W, H)
+    views = synth.random_poses(s, 3, seed=8)
+    fs = [0.5, 1.0, 1.5]
+    r = room_renderer
+    r.render_batch(views, intr, W, H, nl, fs)
+    r.set_timing(True)
+    try:
+        r.render_batch(views, intr, W, H, nl, fs)
+        t = r.get_timing()
+    finally:
+        r.set_timing(False)
+    nvis = 0
+    for v in views:
+        vp = oracle.view_params(g, v.R, v.C)
+        vis, _ = oracle.cull(g, vp, intr, W, H)
+        nvis += oracle.splat(g, vp, intr, W, H, vis)[1]
+    assert t["visible_points"] == nvis > 0
+    assert t["kernels"] == 3 + 1 + 1 + nl + 2 * (2 * 3 - 1) + 1
+    stages = [t[k] for k in ("cull", "splat", "resolve_pyramid", "upsample_pack", "unet")]
+    assert all(x > 0 for x in stages)
+    assert abs(sum(stages) - t["frame"]) <= 0.01
+
+
 def test_device_output_and_torch_stream(lnr, room, room_renderer):
     import torch
     s, g = room
