@@ -136,9 +136,9 @@ def peaks():
 # describes the conv kernels as captured: reported only while their sources are unchanged.
 CONV_TRAFFIC = {"bytes_per_step": 10317.9e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "11b2ad7b144da040c988280b3828f38f41a7449bc72a912e41af53c60451fcd6",
+                           "88506afd4ed6bbd845e467506e703d9e031adb9073c3f14895dc48e14515afaa",
                            "paper_2502_11618_gb300/csrc/unet.cu":
-                           "50b2e4b682991f0ce99dbc367162030fad168bac7175a93ff244f18119f9eecc"}}
+                           "73ac1bad49f33b6771b5bc4f2b055aa06029aa1f464c4a4de00f1f36b4621dc2"}}
 
 
 def conv_traffic():
