@@ -848,11 +848,18 @@ def main():
 
     def serve_run(precision, max_batch, slots, n, lam, seed):
         """n 1080p requests (all at once when lam is None, else Poisson arrivals at rate
-        lam) after a warm-up of the configuration; frames/s and latencies (ms)."""
-        serve_stream(r, lnr, synth, req_list(2 * max_batch * slots, None, seed, 0), precision, max_batch, slots,
-                     False)
-        fps, lat, st = serve_stream(r, lnr, synth, req_list(n, lam, seed, 1000), precision, max_batch, slots,
-                                    lam is not None)
+        lam) after a warm-up of the configuration in the same serving session; frames/s and
+        latencies (ms).  The warm-up gives every slot about eight full batches, so that each
+        slot's frame graphs (one per view block) are captured before the clock starts."""
+        r.set_precision(precision)
+        r.serve_start(max_batch=max_batch, slots=slots)
+        try:
+            serve_stream(r, lnr, synth, req_list(8 * max_batch * slots, None, seed, 0), precision, max_batch, slots,
+                         False, session=False)
+            fps, lat, st = serve_stream(r, lnr, synth, req_list(n, lam, seed, 1000), precision, max_batch, slots,
+                                        lam is not None, session=False)
+        finally:
+            r.serve_stop()
         return fps, np.asarray(lat), st
 
     lam = 0.7 * plain_fps                      # both paths stable at this arrival rate

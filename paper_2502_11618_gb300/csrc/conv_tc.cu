@@ -496,7 +496,7 @@ __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint3
         : "memory");
 }
 
-// 16 channels of one pixel: BF16 (32 bytes) or E4M3 of v * inv (16 bytes, saturating).
+// 16 channels of one pixel as E4M3 of v * inv (16 bytes, saturating).
 __device__ __forceinline__ void st_fp8x16(uint8_t* dst, const float* v, float inv) {
     uint4 pk;
     uint16_t* ph = reinterpret_cast<uint16_t*>(&pk);
@@ -513,29 +513,36 @@ __device__ __forceinline__ void st_32b(void* dst, uint4 a, uint4 b) {
                  : "memory");
 }
 
-__device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
-    uint4 pk[2];
+// ReLU of 16 values, rounded to BF16 and packed two per word (lower half the even element).
+// The conversion applies the ReLU (cvt.rn.relu.bf16x2.f32): the same BF16 values as
+// rounding fmaxf(v, 0), in 8 instructions instead of 16 + 8.
+__device__ __forceinline__ void relu_bf16x16(const float* v, uint4 (&pk)[2]) {
     uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        pw[j] = *reinterpret_cast<uint32_t*>(&b2);
-    }
-    // one 32-byte store (dst is 32-byte aligned: 16 channels at a multiple of 16)
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(pw[0]), "r"(pw[1]), "r"(pw[2]),
-                 "r"(pw[3]), "r"(pw[4]), "r"(pw[5]), "r"(pw[6]), "r"(pw[7])
-                 : "memory");
+    for (int j = 0; j < 8; ++j) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(pw[j]) : "f"(v[2 * j + 1]), "f"(v[2 * j]));
+}
+// Bias + ReLU of 16 FP32 accumulator columns as BF16 pairs; keep = false gives zeros.
+__device__ __forceinline__ void bias_relu_bf16x16(const uint32_t (&u)[16], const float* bias, bool keep, uint4 (&pk)[2]) {
+    float f[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(u[j]) + bias[j];
+    relu_bf16x16(f, pk);
+    if (!keep) pk[0] = pk[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+// 32 packed bytes to a 32-byte-aligned global address.
+__device__ __forceinline__ void st_pk32(void* dst, const uint4 (&pk)[2]) { st_32b(dst, pk[0], pk[1]); }
+// ReLU of 16 values, stored as 16 BF16 channels (32 bytes, 32-byte aligned).
+__device__ __forceinline__ void st_relu_bf16x16(__nv_bfloat16* dst, const float* v) {
+    uint4 pk[2];
+    relu_bf16x16(v, pk);
+    st_32b(dst, pk[0], pk[1]);
+}
+__device__ __forceinline__ void relu16(float (&f)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) f[j] = fmaxf(f[j], 0.f);
 }
 
-// 16 channels packed for a 16-byte-chunk store: BF16 (two chunks) or E4M3 of v * inv (one).
-__device__ __forceinline__ void pack_bf16x16(const float* v, uint4 (&pk)[2]) {
-    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        pw[j] = *reinterpret_cast<uint32_t*>(&b2);
-    }
-}
+// 16 channels as E4M3 of v * inv (one 16-byte chunk, saturating).
 __device__ __forceinline__ uint4 pack_fp8x16(const float* v, float inv) {
     uint4 pk;
     uint16_t* ph = reinterpret_cast<uint16_t*>(&pk);
@@ -934,6 +941,26 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                 }
             }
         };
+        // the same before the ReLU: BF16 outputs take the ReLU in their conversion
+        // (relu_bf16x16); E4M3 outputs and the head apply relu16 first
+        auto pre16 = [&](const uint32_t (&u)[16], int c, float (&f)[16]) {
+            const float4* b4 = reinterpret_cast<const float4*>(p.cbias + c);
+            const float4* s4 = reinterpret_cast<const float4*>(p.cscale + c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 bv = b4[j];
+                const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+                if (IN8) {
+                    const float4 sv = s4[j];
+                    const float ss[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) f[4 * j + i] = fmaf(__uint_as_float(u[4 * j + i]), ss[i], bb[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) f[4 * j + i] = __uint_as_float(u[4 * j + i]) + bb[i];
+                }
+            }
+        };
         int tcount = 0;
         int oc = 0;  // rows (row pairs) this warp has staged: selects the staging buffer
         for (int t = blockIdx.x; tile_live(t); t += gridDim.x, ++tcount) {
@@ -977,14 +1004,20 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                         tmem_ld16_async(trow + (uint32_t)((r + 1) * N + c0), u1);
                         tmem_wait16(u0);
                         tmem_wait16(u1);
+                        // the 2x2 maximum before the ReLU gives the same pooled values
                         float f0[16], f1[16], pm[16];
-                        act16(u0, c0, f0);
-                        act16(u1, c0, f1);
+                        pre16(u0, c0, f0);
+                        pre16(u1, c0, f1);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const float a = fmaxf(f0[j], f1[j]);
                             pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                         }
+                        if (p.out_fp8) {
+                            relu16(f0);
+                            relu16(f1);
+                        }
+                        if (p.pool_fp8) relu16(pm);
                         if (p.ostage) {
                             const uint32_t eo = p.out_fp8 ? 1u : 2u, epb = p.pool_fp8 ? 1u : 2u;
                             auto stage_row = [&](uint32_t buf, const float* f) {
@@ -994,7 +1027,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                                             pack_fp8x16(f, p.inv_out), p.omask);
                                 } else {
                                     uint4 pk[2];
-                                    pack_bf16x16(f, pk);
+                                    relu_bf16x16(f, pk);
 #pragma unroll
                                     for (int h2 = 0; h2 < 2; ++h2) {
                                         const uint32_t cb = (uint32_t)(c0 + 8 * h2) * eo;
@@ -1013,7 +1046,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                                             pack_fp8x16(pm, p.inv_out), p.pmask);
                                 } else {
                                     uint4 pk[2];
-                                    pack_bf16x16(pm, pk);
+                                    relu_bf16x16(pm, pk);
 #pragma unroll
                                     for (int h2 = 0; h2 < 2; ++h2) {
                                         const uint32_t cb = (uint32_t)(c0 + 8 * h2) * epb;
@@ -1031,12 +1064,12 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                             if (v0) st_fp8x16(static_cast<uint8_t*>(p.out) + e0, f0, p.inv_out);
                             if (v1) st_fp8x16(static_cast<uint8_t*>(p.out) + e1, f1, p.inv_out);
                         } else {
-                            if (v0) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e0, f0);
-                            if (v1) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e1, f1);
+                            if (v0) st_relu_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e0, f0);
+                            if (v1) st_relu_bf16x16(static_cast<__nv_bfloat16*>(p.out) + e1, f1);
                         }
                         if ((m & 1) == 0 && v1) {
                             if (p.pool_fp8) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + ep, pm, p.inv_out);
-                            else st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
+                            else st_relu_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + ep, pm);
                         }
                     }
                     if (p.ostage) {  // both rows and the pooled row leave by TMA (clipped at the image edges)
@@ -1137,8 +1170,12 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                         tmem_wait16(u0);
                         if (two) tmem_wait16(u1);
                         float f0[16], f1[16];
-                        act16(u0, c0, f0);
-                        if (two) act16(u1, c0 + 16, f1);
+                        pre16(u0, c0, f0);
+                        if (two) pre16(u1, c0 + 16, f1);
+                        if (p.out_fp8 || p.head_out) {
+                            relu16(f0);
+                            if (two) relu16(f1);
+                        }
                         if (p.ostage) {
                             const uint32_t eo = p.out_fp8 ? 1u : 2u;
                             for (int hf = 0; hf < (two ? 2 : 1); ++hf) {
@@ -1150,7 +1187,7 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                                             pack_fp8x16(f, p.inv_out), p.omask);
                                 } else {
                                     uint4 pk[2];
-                                    pack_bf16x16(f, pk);
+                                    relu_bf16x16(f, pk);
 #pragma unroll
                                     for (int h2 = 0; h2 < 2; ++h2) {
                                         const uint32_t cb = (uint32_t)(cf + 8 * h2) * eo;
@@ -1184,8 +1221,8 @@ __global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const _
                                 else
                                     st_fp8x16(d8, f0, p.inv_out);
                             } else {
-                                st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0, f0);
-                                if (two) st_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0 + 16, f1);
+                                st_relu_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0, f0);
+                                if (two) st_relu_bf16x16(static_cast<__nv_bfloat16*>(p.out) + pix * N + c0 + 16, f1);
                             }
                         }
                     }
@@ -1406,18 +1443,21 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_con
                 const int y = y0 - 1 + r;
                 const bool inside = x >= 0 && x < p.W && y >= 0 && y < p.H;
                 const uint32_t trow = accA + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * N1);
-                for (int c0 = 0; c0 < N1; c0 += 16) {
-                    uint32_t u[16];
-                    tmem_ld16_async(trow + (uint32_t)c0, u);
-                    tmem_wait16(u);
-                    float f[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) f[j] = inside ? fmaxf(__uint_as_float(u[j]) + p.b1[c0 + j], 0.f) : 0.f;
-                    uint4 pk[2];
-                    pack_bf16x16(f, pk);
-                    const uint32_t off = (uint32_t)(r * kHaloW + m) * p.pitch1 + (uint32_t)c0 * 2;
-                    sts_swz(buf, off, pk[0], p.smask1);
-                    sts_swz(buf, off + 16, pk[1], p.smask1);
+                const uint32_t off = (uint32_t)(r * kHaloW + m) * p.pitch1;
+                // both 16-column halves of the row in flight before one wait (N1 is 16 or 32)
+                uint32_t u0[16], u1[16];
+                tmem_ld16_async(trow, u0);
+                if (N1 > 16) tmem_ld16_async(trow + 16u, u1);
+                tmem_wait16(u0);
+                uint4 pk[2];
+                bias_relu_bf16x16(u0, p.b1, inside, pk);
+                sts_swz(buf, off, pk[0], p.smask1);
+                sts_swz(buf, off + 16, pk[1], p.smask1);
+                if (N1 > 16) {
+                    tmem_wait16(u1);
+                    bias_relu_bf16x16(u1, p.b1 + 16, inside, pk);
+                    sts_swz(buf, off + 32, pk[0], p.smask1);
+                    sts_swz(buf, off + 48, pk[1], p.smask1);
                 }
             }
             tc_fence_before();
@@ -1452,20 +1492,35 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_con
                     tmem_ld16_async(tb + (uint32_t)((r + 1) * N2 + c0), u1);
                     tmem_wait16(u0);
                     tmem_wait16(u1);
+                    // ReLU is applied by the BF16 conversions; the 2x2 maximum is taken before
+                    // it, which gives the same pooled values (ReLU is monotone)
                     float f0[16], f1[16], pm[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        f0[j] = fmaxf(__uint_as_float(u0[j]) + p.b2[c0 + j], 0.f);
-                        f1[j] = fmaxf(__uint_as_float(u1[j]) + p.b2[c0 + j], 0.f);
+                        f0[j] = __uint_as_float(u0[j]) + p.b2[c0 + j];
+                        f1[j] = __uint_as_float(u1[j]) + p.b2[c0 + j];
                         const float a = fmaxf(f0[j], f1[j]);
                         pm[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
                     }
-                    if (vx && y < p.H) st_bf16x16(p.out + (((size_t)n * p.H + y) * p.W + x) * N2 + c0, f0);
-                    if (vx && y + 1 < p.H) st_bf16x16(p.out + (((size_t)n * p.H + y + 1) * p.W + x) * N2 + c0, f1);
+                    uint4 pk[2];
+                    if (vx && y < p.H) {
+                        relu_bf16x16(f0, pk);
+                        st_pk32(p.out + (((size_t)n * p.H + y) * p.W + x) * N2 + c0, pk);
+                    }
+                    if (vx && y + 1 < p.H) {
+                        relu_bf16x16(f1, pk);
+                        st_pk32(p.out + (((size_t)n * p.H + y + 1) * p.W + x) * N2 + c0, pk);
+                    }
                     if (vx && (m & 1) == 0 && y + 1 < p.H) {
                         const size_t pp = (((size_t)n * Hh + (y >> 1)) * Wh + (x >> 1)) * N2 + c0;
-                        if (p.pool8) st_fp8x16(static_cast<uint8_t*>(p.pool_out) + pp, pm, p.inv_pool);
-                        else st_bf16x16(static_cast<__nv_bfloat16*>(p.pool_out) + pp, pm);
+                        if (p.pool8) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) pm[j] = fmaxf(pm[j], 0.f);
+                            st_fp8x16(static_cast<uint8_t*>(p.pool_out) + pp, pm, p.inv_pool);
+                        } else {
+                            relu_bf16x16(pm, pk);
+                            st_pk32(static_cast<__nv_bfloat16*>(p.pool_out) + pp, pk);
+                        }
                     }
                 }
             }

@@ -111,6 +111,19 @@ def test_batch_equals_single(lnr, room, room_renderer):
         assert np.array_equal(yb[i], y1)
 
 
+def test_batch_beyond_one_splat_launch(lnr, room, room_renderer):
+    """A batch of more views than one splat launch covers (64): views on either side of
+    the boundary equal the same views rendered alone, bit for bit."""
+    s, g = room
+    W, H, nl = 64, 48, 2
+    intr = synth.intrinsics_for(W, H)
+    views = synth.random_poses(s, 67, seed=21)
+    fs = [0.5 + (i % 3) * 0.5 for i in range(67)]
+    yb = room_renderer.render_batch(views, intr, W, H, nl, fs)
+    for i in (0, 1, 63, 64, 65, 66):
+        assert np.array_equal(yb[i], room_renderer.render(views[i], intr, W, H, nl, fs[i])), i
+
+
 def test_timing_reports_visible_points_and_launches(lnr, room, room_renderer):
     """lnr_get_timing after a timed batch: stage times that add up to the frame's, the
     batch's visible points (the oracle's splat count summed over the views) and the frame's
