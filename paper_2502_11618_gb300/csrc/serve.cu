@@ -1,13 +1,15 @@
 // Serving loop: continuous batching of render requests on one GPU.
 //
 // Requests (pose, resolution, n_levels, filter_strength) are queued by lnr_submit from any
-// thread.  A scheduler thread owns `slots` workspaces, each with its own CUDA stream and
-// buffers.  Whenever a slot is free it takes the oldest queued request and up to
-// max_batch - 1 more of the same resolution and pyramid depth, admits them if their
-// activation memory fits the budget next to the requests already on the GPU, and launches
-// the batch (a replayed CUDA graph once the configuration has been seen) followed by the
-// device-to-host copy of every result into its own pinned buffer and an event.  Work of
-// different slots overlaps on the device.  Completed requests are picked up by lnr_poll.
+// thread.  A scheduler thread owns `slots` workspaces with their buffers.  Whenever a slot
+// is free it takes the oldest queued request and up to max_batch - 1 more of the same
+// resolution and pyramid depth, admits them if their activation memory fits the budget next
+// to the requests already on the GPU, and launches the batch (a replayed CUDA graph once the
+// configuration has been seen).  The frames of all slots run in launch order on one compute
+// stream: the conv kernels are persistent (one CTA per SM), and two frames sharing the SMs
+// would leave each with part of the GPU and a long tail.  The device-to-host copy of every
+// result, into its own pinned buffer, goes on the slot's copy stream after its frame, and
+// overlaps the next frames.  Completed requests are picked up by lnr_poll.
 //
 // Memory: a slot's buffers grow to the largest batch it has run.  Under a budget
 // (lnr_set_memory_budget) admission counts the bytes the slots actually hold: a batch is
@@ -25,8 +27,10 @@
 namespace lnr {
 
 struct Slot {
-    Workspace ws;
-    cudaEvent_t done = nullptr;
+    Workspace ws;                     // ws.stream is the server's compute stream (not owned)
+    cudaStream_t copy = nullptr;      // the results' device-to-host copies
+    cudaEvent_t computed = nullptr;   // the frame is done on the compute stream
+    cudaEvent_t done = nullptr;       // and its results are in host memory
     std::vector<uint64_t> tickets;
     bool busy = false;
 };
@@ -138,6 +142,7 @@ struct ServeReq {
 struct Server {
     lnr_ctx* c = nullptr;
     int max_batch = 1;
+    cudaStream_t compute = nullptr;  // every slot's frames, in launch order
     std::vector<std::unique_ptr<Slot>> slots;
     std::mutex mu;
     std::condition_variable cv;
@@ -231,10 +236,13 @@ bool Server::launch(Slot& s, std::vector<uint64_t>& batch, size_t need) {
                 dst = r.host;
             }
         }
-        if (!dst || cudaMemcpyAsync(dst, s.ws.out.as<float>() + i * per, per * 4, cudaMemcpyDeviceToHost, s.ws.stream))
+        if (i == 0 && (cudaEventRecord(s.computed, s.ws.stream) != cudaSuccess ||
+                       cudaStreamWaitEvent(s.copy, s.computed, 0) != cudaSuccess))
+            return false;
+        if (!dst || cudaMemcpyAsync(dst, s.ws.out.as<float>() + i * per, per * 4, cudaMemcpyDeviceToHost, s.copy))
             return false;
     }
-    if (cudaEventRecord(s.done, s.ws.stream) != cudaSuccess) return false;
+    if (cudaEventRecord(s.done, s.copy) != cudaSuccess) return false;
     s.tickets = batch;
     s.busy = true;
     return true;
@@ -336,14 +344,27 @@ lnr_status lnr_serve_start(lnr_ctx* c, int max_batch, int nslots) {
     s->c = c;
     s->max_batch = max_batch;
     s->prec = c->prec;
+    if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return fail(c, LNR_E_CUDA, "serving streams");
+    }
     for (int i = 0; i < nslots; ++i) {
         auto sl = std::make_unique<Slot>();
-        if (cudaStreamCreateWithFlags(&sl->ws.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess) {
+        sl->ws.stream = s->compute;
+        const bool ok = cudaStreamCreateWithFlags(&sl->copy, cudaStreamNonBlocking) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&sl->computed, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) == cudaSuccess;
+        s->slots.push_back(std::move(sl));
+        if (!ok) {
+            for (auto& x : s->slots) {
+                if (x->copy) cudaStreamDestroy(x->copy);
+                if (x->computed) cudaEventDestroy(x->computed);
+                if (x->done) cudaEventDestroy(x->done);
+            }
+            cudaStreamDestroy(s->compute);
             delete s;
             return fail(c, LNR_E_CUDA, "serving streams");
         }
-        s->slots.push_back(std::move(sl));
     }
     c->server = s;
     s->copier.start();
@@ -362,18 +383,24 @@ lnr_status lnr_serve_stop(lnr_ctx* c) {
     lnr_status st = LNR_OK;
     cudaSetDevice(c->device);
     const double deadline = now_s() + 10.0;
-    for (auto& sl : s->slots) {
-        while (cudaStreamQuery(sl->ws.stream) == cudaErrorNotReady) {
+    auto drain = [&](cudaStream_t q) {
+        while (st == LNR_OK && cudaStreamQuery(q) == cudaErrorNotReady) {
             if (now_s() > deadline) {
                 st = fail(c, LNR_E_TIMEOUT, "serving stop: device work did not finish in 10 s");
                 break;
             }
             std::this_thread::sleep_for(std::chrono::microseconds(100));
         }
+    };
+    drain(s->compute);
+    for (auto& sl : s->slots) drain(sl->copy);
+    for (auto& sl : s->slots) {
         sl->ws.release();
-        cudaStreamDestroy(sl->ws.stream);
+        cudaStreamDestroy(sl->copy);
+        cudaEventDestroy(sl->computed);
         cudaEventDestroy(sl->done);
     }
+    cudaStreamDestroy(s->compute);
     for (auto& kv : s->reqs)
         if (kv.second.host) cudaFreeHost(kv.second.host);
     s->pool.release();
