@@ -570,6 +570,10 @@ __device__ __forceinline__ void sts_swz(uint32_t buf, uint32_t off, uint4 v, uin
     const uint32_t ph = a ^ (((a >> 7) & mask) << 4);
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ph), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
+// 16 bytes at an already swizzled shared-memory address.
+__device__ __forceinline__ void sts16(uint32_t a, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, uint32_t src, int c0, int c1, int c2, int c3) {
     asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"((uint64_t)m),
@@ -1443,7 +1447,9 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_con
                 const int y = y0 - 1 + r;
                 const bool inside = x >= 0 && x < p.W && y >= 0 && y < p.H;
                 const uint32_t trow = accA + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * N1);
-                const uint32_t off = (uint32_t)(r * kHaloW + m) * p.pitch1;
+                // the pixel's 32 or 64 bytes lie in one 128-byte line: one swizzle pattern
+                const uint32_t a = buf + (uint32_t)(r * kHaloW + m) * p.pitch1;
+                const uint32_t sx = ((a >> 7) & p.smask1) << 4;
                 // both 16-column halves of the row in flight before one wait (N1 is 16 or 32)
                 uint32_t u0[16], u1[16];
                 tmem_ld16_async(trow, u0);
@@ -1451,13 +1457,13 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_con
                 tmem_wait16(u0);
                 uint4 pk[2];
                 bias_relu_bf16x16(u0, p.b1, inside, pk);
-                sts_swz(buf, off, pk[0], p.smask1);
-                sts_swz(buf, off + 16, pk[1], p.smask1);
+                sts16(a ^ sx, pk[0]);
+                sts16((a + 16) ^ sx, pk[1]);
                 if (N1 > 16) {
                     tmem_wait16(u1);
                     bias_relu_bf16x16(u1, p.b1 + 16, inside, pk);
-                    sts_swz(buf, off + 32, pk[0], p.smask1);
-                    sts_swz(buf, off + 48, pk[1], p.smask1);
+                    sts16((a + 32) ^ sx, pk[0]);
+                    sts16((a + 48) ^ sx, pk[1]);
                 }
             }
             tc_fence_before();
