@@ -131,12 +131,12 @@ def peaks():
 
 
 # DRAM traffic (read + write bytes) of all U-Net conv launches of one step of this workload
-# (8 x 1080p views, BF16): ncu DRAM counters of the twelve separate conv launches at 2 views
-# (x 4) and of the fused level-0 encoder at 1 view (x 8), scaled by the views processed.  It
-# describes the conv kernels as captured: reported only while their sources are unchanged.
-CONV_TRAFFIC = {"bytes_per_step": 10317.9e6,
+# (8 x 1080p views, BF16): ncu DRAM counters of the 13 conv launches of a 2-view step, x 4
+# (scaled by the views processed).  It describes the conv kernels as captured: reported
+# only while their sources are unchanged.
+CONV_TRAFFIC = {"bytes_per_step": 10544.5e6,
                 "sha256": {"paper_2502_11618_gb300/csrc/conv_tc.cu":
-                           "88506afd4ed6bbd845e467506e703d9e031adb9073c3f14895dc48e14515afaa",
+                           "4c41dc937e1a23b388458e0c30d6c4d0d05f849d5d58b723fc81e6d92ed72b20",
                            "paper_2502_11618_gb300/csrc/unet.cu":
                            "73ac1bad49f33b6771b5bc4f2b055aa06029aa1f464c4a4de00f1f36b4621dc2"}}
 
@@ -795,8 +795,8 @@ def main():
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = conv_traffic() if have_tc else None
-    roof["traffic_scope"] = ("DRAM bytes read + written by all U-Net conv launches of one step (ncu at 2 views and, "
-                             "for the fused level-0 encoder, 1 view; scaled by the views processed)")
+    roof["traffic_scope"] = ("DRAM bytes read + written by all U-Net conv launches of one step (ncu at 2 views, "
+                             "scaled by the views processed)")
     roof_stages = stage_roofline(stages, nvis_step, W * H * B, hbm)
     filter_cost = {"n_levels": [0, NLEV],
                    "filter_ms_per_step": [stages0["upsample_pack"], stages["upsample_pack"]],
