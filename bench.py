@@ -394,7 +394,8 @@ def stage_roofline(stage_ms, nvis, n_px, hbm_gbs):
 
 def percentiles(lat_ms):
     a = np.asarray(lat_ms, np.float64)
-    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+    return {"p50": float(np.percentile(a, 50)), "p90": float(np.percentile(a, 90)), "p99": float(np.percentile(a, 99)),
+            "max": float(a.max())}
 
 
 _PINNED = {}   # (W, H) -> free page-locked result buffers, reused across serving runs
