@@ -1455,26 +1455,21 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_enc0_fused(const __grid_con
                 tmem_ld16_async(trow, u0);
                 if (N1 > 16) tmem_ld16_async(trow + 16u, u1);
                 tmem_wait16(u0);
-                if (N1 > 16) tmem_wait16(u1);
-                if (r + 2 >= R + 2) {
-                    // this warp's last row is in registers: the next tile's first conv may
-                    // overwrite the accumulators while the row is converted and stored
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(a_empty);
-                }
                 uint4 pk[2];
                 bias_relu_bf16x16(u0, p.b1, inside, pk);
                 sts16(a ^ sx, pk[0]);
                 sts16((a + 16) ^ sx, pk[1]);
                 if (N1 > 16) {
+                    tmem_wait16(u1);
                     bias_relu_bf16x16(u1, p.b1 + 16, inside, pk);
                     sts16((a + 32) ^ sx, pk[0]);
                     sts16((a + 48) ^ sx, pk[1]);
                 }
             }
+            tc_fence_before();
             fence_async_smem();  // the tensor cores read these activations
             __syncwarp();
+            if (lane == 0) mbar_arrive(a_empty);
             named_sync(1, 256);
             if (leader) mbar_arrive(act_full(ab));
         }
