@@ -572,11 +572,11 @@ def run_100M(args, lnr, synth, torch, dev, B):
     return res
 
 
-def density_sweep(lnr, synth, torch, dev, scene, B, fractions=(0.1, 0.25, 0.5)):
+def density_sweep(lnr, synth, torch, dev, scene, B, fractions=(0.05, 0.1, 0.25, 0.5)):
     """Output sensitivity (the paper's claim that cost follows the visible points, Sec. 1):
-    the multiroom_20M scan decimated to a seeded subset of its points, 8 x 1080p views per
-    step, BF16; per configuration visible points per view, raster and U-Net time (library
-    stage events) and frames/s."""
+    the multiroom_20M scan decimated to a seeded subset of its points (1M to 10M), 8 x 1080p
+    views per step, BF16; per configuration the visible points per view and per second of
+    frame time, raster and U-Net time (library stage events) and frames/s."""
     weights = synth.unet_weights(CH, seed=1)
     intr = synth.intrinsics_for(W, H)
     views = synth.random_poses(scene, N_POSES, seed=2)
@@ -590,7 +590,6 @@ def density_sweep(lnr, synth, torch, dev, scene, B, fractions=(0.1, 0.25, 0.5)):
             r.build_grid(CELL)
             r.set_unet(CH, weights, "bf16")
             r.autotune(W, H, B)
-            vis = [r.render_stage(v, intr, W, H, NLEV, 1.0, lnr.STAGE_CULL)[1] for v in views[:B]]
             fs = [FS[k % 2] for k in range(B)]
             for _ in range(3):
                 r.render_batch(views[:B], intr, W, H, NLEV, fs)
@@ -604,7 +603,9 @@ def density_sweep(lnr, synth, torch, dev, scene, B, fractions=(0.1, 0.25, 0.5)):
             r.close()
         med = lambda k: float(np.median([t[k] for t in tims]))
         raster = med("cull") + med("splat") + med("resolve_pyramid") + med("upsample_pack")
-        out.append({"points": int(len(keep)), "fraction": frac, "visible_points_per_view": float(np.mean(vis)),
+        nvis = float(np.mean([t["visible_points"] for t in tims]))   # per step, the library's count
+        out.append({"points": int(len(keep)), "fraction": frac, "visible_points_per_view": nvis / B,
+                    "visible_points_per_s": nvis / (med("frame") * 1e-3),
                     "raster_ms_per_step": raster, "splat_ms_per_step": med("splat"), "unet_ms_per_step": med("unet"),
                     "frames_per_s": B / (med("frame") * 1e-3)})
     return out
@@ -911,6 +912,7 @@ def main():
     if have_tc and rank == 0 and world == 1 and not args.no_extras:
         sweep = density_sweep(lnr, synth, torch, dev, scene, B)
         sweep.append({"points": N_POINTS, "fraction": 1.0, "visible_points_per_view": nvis_step / B,
+                      "visible_points_per_s": nvis_step / (stages["frame"] * 1e-3),
                       "raster_ms_per_step": stages["cull"] + stages["splat"] + stages["resolve_pyramid"] +
                       stages["upsample_pack"], "splat_ms_per_step": stages["splat"],
                       "unet_ms_per_step": stages["unet"], "frames_per_s": B / (stages["frame"] * 1e-3)})
