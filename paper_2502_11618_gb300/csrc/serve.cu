@@ -322,8 +322,17 @@ void Server::loop() {
             progressed = true;
         }
         if (!progressed) {
-            std::unique_lock<std::mutex> lk(mu);
-            cv.wait_for(lk, std::chrono::microseconds(20));
+            bool in_flight = false;
+            for (const auto& sp : slots) in_flight = in_flight || sp->busy;
+            if (in_flight) {
+                // frames on the device: poll their events without sleeping.  A thread that
+                // sleeps can take milliseconds to run again on a loaded host, and the GPU
+                // idles until the next batch is launched.
+                std::this_thread::yield();
+            } else {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait_for(lk, std::chrono::microseconds(500), [&] { return stop.load() || !queue.empty(); });
+            }
         }
     }
 }
