@@ -450,17 +450,17 @@ def serve_stream(r, lnr, synth, reqs, precision, max_batch, slots, realtime, win
                 pending.append((r.submit_into(q.view, synth.intrinsics_for(q.W, q.H), q.W, q.H, q.n_levels, q.fs, b),
                                 b, (q.W, q.H)))
                 i += 1
-            # results complete roughly in submission order: poll the oldest ones until one is
-            # still in flight
-            done = 0
+            # poll every outstanding request: a batch whose results arrive late then holds
+            # only its own requests, and the window keeps refilling behind it
+            still = []
             for tk, b, key in pending:
                 res, l = r.poll(tk)
                 if l is None:
-                    break
-                lat.append(1e3 * l)
-                pools[key].append(b)
-                done += 1
-            pending = pending[done:]
+                    still.append((tk, b, key))
+                else:
+                    lat.append(1e3 * l)
+                    pools[key].append(b)
+            pending = still
         span = time.perf_counter() - t0
         st = r.serve_stats()
         nl = st["launches"] - st0["launches"]
