@@ -231,8 +231,11 @@ lnr_status lnr_autotune(lnr_ctx* ctx, int W, int H, int batch);
 /* ---- serving: continuous batching of render requests ------------------------------ */
 
 /* Start the serving loop: up to max_batch requests of one resolution per launch, up to
- * `slots` launches in flight on separate streams.  Uses the precision selected by
- * set_unet / set_precision at this call. */
+ * `slots` launches in flight.  The frames run in launch order on one compute stream of the
+ * loop; each slot copies its results to host memory on a stream of its own, overlapping
+ * the next frames.  Uses the precision selected by set_unet / set_precision at this call.
+ * Errors: LNR_E_STATE (already serving, or no grid / network), LNR_E_ARG (max_batch
+ * outside [1, 64], slots outside [1, 16]), LNR_E_CUDA. */
 lnr_status lnr_serve_start(lnr_ctx* ctx, int max_batch, int slots);
 lnr_status lnr_serve_stop(lnr_ctx* ctx);
 /* Device-memory budget of the serving loop's slots (0 = no bound): a batch is admitted when
