@@ -38,17 +38,20 @@ namespace lnr {
 namespace {
 
 constexpr int kThreads = 192;
-// halo kernel: producer warp, MMA-issuing warps (kMmaWarps for the decoder's concat convs,
-// whose tiles hold up to four independent units; two for standard tiles, whose rows split
-// between two issuers), then EPI epilogue warps.  One thread issues about one tcgen05.mma
-// per ~120 cycles whatever N is, so small-N convolutions need several issuing threads; each
-// owns disjoint accumulators.
+// halo kernel: producer warp, MMA-issuing warps (one per independent unit of a parity tile
+// of the decoder's concat convs, at most kMmaWarps; two for standard tiles, whose rows split
+// between two issuers), then EPI epilogue warps.  Each issuer owns disjoint accumulators.
+// An issuing thread shares its scheduler with the epilogue warps of its TMEM lane quarter,
+// so small-N convolutions, whose MMAs are short, are issued from several threads.
 constexpr int kMmaWarps = 4;
-__host__ __device__ constexpr int halo_mma_warps(int par) { return par == 0 ? 2 : kMmaWarps; }
-// Epilogue warps, chosen per layer: 4 (one per TMEM lane quarter), 8 or, for standard tiles,
-// 12 (two or three per quarter: more latency hiding for TMEM loads, stores and the fused
-// head's dot products, at 128 registers per thread).
-__host__ __device__ constexpr int halo_threads(int par, int epi) { return 32 * (1 + halo_mma_warps(par) + epi); }
+__host__ __device__ constexpr int halo_mma_warps(int par, int r) {
+    return par == 0 ? 2 : ((par == 4 ? 2 : 1) * r < kMmaWarps ? (par == 4 ? 2 : 1) * r : kMmaWarps);
+}
+// Epilogue warps, chosen per layer: 4 (one per TMEM lane quarter), 8 or 12 (two or three per
+// quarter: more latency hiding for TMEM loads, stores and the fused head's dot products, at
+// 128 registers per thread).  12 for standard tiles and for tiles of two parity classes and
+// at most two rows, whose two issuers leave room for them.
+__host__ __device__ constexpr int halo_threads(int par, int r, int epi) { return 32 * (1 + halo_mma_warps(par, r) + epi); }
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr long long kStallWaitCycles = 2000000ll;  // ~1 ms: the timeout test's wait
 constexpr int kXchStride = 33;                   // floats per row of the pooling exchange
@@ -764,8 +767,8 @@ __device__ __forceinline__ void issue_stage(const IssueCtx& q, int sg, uint32_t 
 // (x mod 2, y mod 2) of the fine pixels above them: 1 class, both x classes of one y
 // class, or all four.  The tile's PAR*R accumulators share every staged halo and weight.
 template <int R, int PAR, bool IN8, int EPI>
-__global__ void __launch_bounds__(halo_threads(PAR, EPI), 1) k_conv_halo(const __grid_constant__ HParams p) {
-    constexpr int MW = halo_mma_warps(PAR);
+__global__ void __launch_bounds__(halo_threads(PAR, R, EPI), 1) k_conv_halo(const __grid_constant__ HParams p) {
+    constexpr int MW = halo_mma_warps(PAR, R);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -2010,7 +2013,9 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         p.ntiles = B * p.tiles_y * p.tiles_x;
     }
     p.stage_bytes = stage;
-    const int epi = E == 4 ? 4 : (E == 12 && P == 0) ? 12 : 8;  // epilogue warps (12: standard tiles only)
+    // epilogue warps: 12 for standard tiles and for tiles of two parity classes and at most
+    // two rows (the decoder's full- and quarter-resolution concat convs)
+    const int epi = E == 4 ? 4 : (E == 12 && (P == 0 || (P == 2 && R <= 2))) ? 12 : 8;
     // epilogue stores through staging + TMA (no fused head: its outputs are per-pixel floats)
     uint32_t stg_total = 0;
     if (O) {
@@ -2116,17 +2121,17 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
         constexpr int PP = decltype(par)::value, EE = decltype(ep)::value;
         if (ty.in8) {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, true, EE>, halo_threads(PP, EE)); break;
-                case 2: launch(k_conv_halo<2, PP, true, EE>, halo_threads(PP, EE)); break;
-                case 4: launch(k_conv_halo<4, PP, true, EE>, halo_threads(PP, EE)); break;
-                default: launch(k_conv_halo<8, PP, true, EE>, halo_threads(PP, EE)); break;
+                case 1: launch(k_conv_halo<1, PP, true, EE>, halo_threads(PP, 1, EE)); break;
+                case 2: launch(k_conv_halo<2, PP, true, EE>, halo_threads(PP, 2, EE)); break;
+                case 4: launch(k_conv_halo<4, PP, true, EE>, halo_threads(PP, 4, EE)); break;
+                default: launch(k_conv_halo<8, PP, true, EE>, halo_threads(PP, 8, EE)); break;
             }
         } else {
             switch (R) {
-                case 1: launch(k_conv_halo<1, PP, false, EE>, halo_threads(PP, EE)); break;
-                case 2: launch(k_conv_halo<2, PP, false, EE>, halo_threads(PP, EE)); break;
-                case 4: launch(k_conv_halo<4, PP, false, EE>, halo_threads(PP, EE)); break;
-                default: launch(k_conv_halo<8, PP, false, EE>, halo_threads(PP, EE)); break;
+                case 1: launch(k_conv_halo<1, PP, false, EE>, halo_threads(PP, 1, EE)); break;
+                case 2: launch(k_conv_halo<2, PP, false, EE>, halo_threads(PP, 2, EE)); break;
+                case 4: launch(k_conv_halo<4, PP, false, EE>, halo_threads(PP, 4, EE)); break;
+                default: launch(k_conv_halo<8, PP, false, EE>, halo_threads(PP, 8, EE)); break;
             }
         }
     };
@@ -2140,7 +2145,19 @@ bool tc_conv_halo(const ConvLayer& L, const void* src0, const void* src1, void* 
             else pick(std::integral_constant<int, 0>{});
             break;
         case 1: pick(std::integral_constant<int, 1>{}); break;
-        case 2: pick(std::integral_constant<int, 2>{}); break;
+        case 2:
+            if (epi == 12) {  // R is 1 or 2 here
+                if (ty.in8) {
+                    if (R == 1) launch(k_conv_halo<1, 2, true, 12>, halo_threads(2, 1, 12));
+                    else launch(k_conv_halo<2, 2, true, 12>, halo_threads(2, 2, 12));
+                } else {
+                    if (R == 1) launch(k_conv_halo<1, 2, false, 12>, halo_threads(2, 1, 12));
+                    else launch(k_conv_halo<2, 2, false, 12>, halo_threads(2, 2, 12));
+                }
+            } else {
+                pick(std::integral_constant<int, 2>{});
+            }
+            break;
         default: pick(std::integral_constant<int, 4>{}); break;
     }
     return true;
@@ -2351,7 +2368,7 @@ std::vector<TcConfig> tc_candidates(const ConvLayer& L, lnr_precision prec) {
                 const uint32_t sb = halo_stage_bytes(L, r, P, ck, esize);
                 if (sb * 2 > 220u * 1024u) continue;
                 for (int e : {4, 8, 12}) {
-                    if (e == 12 && P) continue;  // 12 epilogue warps: standard tiles only
+                    if (e == 12 && P && !(P == 2 && r <= 2)) continue;  // 12 epilogue warps: see the launch
                     TcConfig c;
                     c.mode = 1;
                     c.R = r;
